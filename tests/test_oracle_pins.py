@@ -1,0 +1,407 @@
+"""Pins for the CPU oracle: values fixed by the paper or by the mathematics.
+
+Each test checks the oracle against something other than itself: the paper's
+Table I, closed forms of the named channels on Bell and GHZ states, brute
+force over basis states, independent constructions of the same object, and
+the invariants every Kraus map has (hermiticity, trace, positivity, spectrum,
+trace duality).  ``test_planted_mistakes_are_caught`` plants typical
+mistakes in the oracle and checks that these pins fail.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dense as D
+from oracle import tiled as T
+from workloads import synth as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+UNITS = {"B": 1, "KiB": 1 << 10, "MiB": 1 << 20, "GiB": 1 << 30}
+
+
+def _parse_size(tok):
+    for u in ("KiB", "MiB", "GiB", "B"):
+        if tok.endswith(u):
+            return float(tok[: -len(u)]) * UNITS[u], tok[: -len(u)]
+    raise ValueError(tok)
+
+
+def _round_like(value_bytes, printed):
+    """Round value (in the printed unit) to the printed number of decimals."""
+    dec = len(printed.split(".")[1]) if "." in printed else 0
+    return round(value_bytes, dec)
+
+
+# ---------------------------------------------------------------- Table I
+def test_table1_memory_footprint():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1_memory_footprint.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append(line.split())
+    assert len(rows) == 5
+    for n_s, full_s, packed_s, tiled_s, ratio_s in rows:
+        n = int(n_s)
+        N = 1 << n
+        full = N * N * 16
+        packed = N * (N + 1) // 2 * 16
+        tiled = T.stored_bytes(n, 5, 16)
+        for val, tok in ((full, full_s), (packed, packed_s), (tiled, tiled_s)):
+            expect, printed = _parse_size(tok)
+            unit = tok[len(printed):]
+            assert _round_like(val / UNITS[unit], printed) == pytest.approx(float(printed)), (n, tok, val)
+        dec = len(ratio_s.split(".")[1]) if "." in ratio_s else 0
+        assert round(tiled / packed, dec) == pytest.approx(float(ratio_s)), (n, tiled / packed)
+
+
+def test_storage_formula_and_padding():
+    for n in range(1, 12):
+        for m in range(0, 7):
+            N, M = 1 << n, 1 << m
+            expect = M * M if N < M else N * (N + M) // 2
+            assert T.stored_elements(n, m) == expect
+
+
+# ---------------------------------------------------------------- layout
+@pytest.mark.parametrize("n,m", [(1, 5), (2, 5), (3, 1), (4, 2), (5, 5), (6, 3), (6, 0), (7, 2)])
+def test_tiled_roundtrip_and_element_map(n, m):
+    rng = S.rng_for(11 + n + 10 * m)
+    H = S.random_hermitian(rng, 1 << n)
+    buf = T.to_tiled(H, m)
+    assert buf.size == T.stored_elements(n, m)
+    assert np.array_equal(T.from_tiled(buf, n, m), H)
+    N = 1 << n
+    for i in range(N):
+        for j in range(N):
+            off, conj = T.element_offset(i, j, n, m)
+            v = np.conj(buf[off]) if conj else buf[off]
+            assert v == H[i, j]
+
+
+def test_m0_is_row_major_packed():
+    """Footnote of Sec. IV-A: m = 0 recovers the packed format up to order."""
+    rng = S.rng_for(5)
+    n = 5
+    H = S.random_hermitian(rng, 1 << n)
+    packed_rows = np.concatenate([H[i, : i + 1] for i in range(1 << n)])
+    assert np.array_equal(T.to_tiled(H, 0), packed_rows)
+
+
+def _extract(g, A):
+    return sum(((g >> p) & 1) << l for l, p in enumerate(sorted(A)))
+
+
+def _compress(g, A, n):
+    rest = [p for p in range(n) if p not in A]
+    return sum(((g >> p) & 1) << l for l, p in enumerate(rest))
+
+
+def test_insert_bits_bruteforce():
+    """Subroutine 1: inserting the bits of a at A into s reproduces every
+    global index, for all subsets A of size 1..3 of n <= 6 bits."""
+    for n in range(1, 7):
+        for k in range(1, min(3, n) + 1):
+            for A in itertools.combinations(range(n), k):
+                for g in range(1 << n):
+                    assert T.insert_bits(_compress(g, A, n), _extract(g, A), A) == g
+
+
+# ---------------------------------------------------------------- embedding
+def _embed_by_definition(L, qubits, n):
+    """K[i, j] = L[a(i), a(j)] if i and j agree outside ``qubits`` else 0,
+    with a(i) the local index whose bit l is bit qubits[l] of i."""
+    N = 1 << n
+    K = np.zeros((N, N), dtype=np.complex128)
+    mask = sum(1 << q for q in qubits)
+    for i in range(N):
+        ai = sum(((i >> q) & 1) << l for l, q in enumerate(qubits))
+        for j in range(N):
+            if (i & ~mask) == (j & ~mask):
+                aj = sum(((j >> q) & 1) << l for l, q in enumerate(qubits))
+                K[i, j] = L[ai, aj]
+    return K
+
+
+def test_embed_matches_definition():
+    rng = S.rng_for(7)
+    n = 4
+    for k in (1, 2, 3):
+        for qubits in itertools.permutations(range(n), k):
+            L = rng.standard_normal((1 << k, 1 << k)) + 1j * rng.standard_normal((1 << k, 1 << k))
+            assert np.array_equal(D.embed(L, qubits, n, sparse=False), _embed_by_definition(L, list(qubits), n))
+
+
+def test_dense_and_sparse_embeddings_agree():
+    rng = S.rng_for(8)
+    for n in (3, 5, 6):
+        for qubits in ([0], [n - 1], [1, n - 1], [n - 1, 0], [2, 1]):
+            L = S.haar_unitary(rng, 1 << len(qubits))
+            Kd = D.embed(L, qubits, n, sparse=False)
+            Ks = D.embed(L, qubits, n, sparse=True).toarray()
+            assert np.array_equal(Kd, Ks)
+
+
+def test_sparse_apply_matches_dense_apply(monkeypatch):
+    rng = S.rng_for(9)
+    n = 6
+    rho = S.ginibre_state(rng, 1 << n)
+    U = S.haar_unitary(rng, 4)
+    dense = D.apply_unitary(rho, U, [1, 4])
+    monkeypatch.setattr(D, "DENSE_MAX_N", 2)
+    sparse = D.apply_unitary(rho, U, [1, 4])
+    assert np.max(np.abs(dense - sparse)) < 1e-15
+
+
+def test_cnot_on_basis_states():
+    """Bit l of a 2-qubit matrix's index is qubits[l]: CNOT with its control
+    on index bit 0 flips qubit qubits[1] exactly when qubit qubits[0] is 1."""
+    cnot = np.zeros((4, 4), dtype=np.complex128)
+    for b in range(4):
+        b0, b1 = b & 1, (b >> 1) & 1
+        cnot[((b1 ^ b0) << 1) | b0, b] = 1
+    n = 4
+    for c, t in itertools.permutations(range(n), 2):
+        for x in range(1 << n):
+            rho = np.zeros((1 << n, 1 << n), dtype=np.complex128)
+            rho[x, x] = 1
+            out = D.apply_unitary(rho, cnot, [c, t])
+            y = x ^ (((x >> c) & 1) << t)
+            expect = np.zeros_like(rho)
+            expect[y, y] = 1
+            assert np.array_equal(out, expect)
+
+
+def test_pauli_x_is_a_pure_swap():
+    """Sec. II-B: X on qubit a swaps h[i,j] with h[i^2^a, j^2^a], bit for bit."""
+    rng = S.rng_for(10)
+    n = 5
+    H = S.random_hermitian(rng, 1 << n)
+    for a in range(n):
+        perm = np.arange(1 << n) ^ (1 << a)
+        assert np.array_equal(D.apply_unitary(H, D.X, [a]), H[np.ix_(perm, perm)])
+
+
+# ---------------------------------------------------------------- channels
+def _depolarizing_closed_form(rho, q, p):
+    """(1 - l) rho + l (I/2 (x)_q tr_q rho) with l = 4p/3, built elementwise."""
+    lam = 4.0 * p / 3.0
+    N = rho.shape[0]
+    out = (1 - lam) * rho.copy()
+    bit = 1 << q
+    for i in range(N):
+        for j in range(N):
+            if ((i ^ j) & bit) == 0:
+                i0, j0 = i & ~bit, j & ~bit
+                out[i, j] += lam * 0.5 * (rho[i0, j0] + rho[i0 | bit, j0 | bit])
+    return out
+
+
+def test_depolarizing_closed_form():
+    rng = S.rng_for(12)
+    n = 4
+    rho = S.ginibre_state(rng, 1 << n)
+    for q in range(n):
+        for p in (0.0, 0.01, 0.1, 0.75):
+            got = D.depolarize(rho, q, p)
+            assert np.max(np.abs(got - _depolarizing_closed_form(rho, q, p))) < 1e-15
+
+
+def _bell():
+    v = np.zeros(4, dtype=np.complex128)
+    v[0] = v[3] = 1 / np.sqrt(2)
+    return np.outer(v, v.conj())
+
+
+def test_bell_depolarized_is_werner():
+    for q in (0, 1):
+        for p in (0.03, 0.1, 0.4):
+            lam = 4 * p / 3
+            rho = D.depolarize(_bell(), q, p)
+            werner = (1 - lam) * _bell() + lam * np.eye(4) / 4
+            assert np.max(np.abs(rho - werner)) < 1e-15
+            assert D.expect_pauli(rho, "XX") == pytest.approx(1 - lam, abs=1e-15)
+            assert D.expect_pauli(rho, "ZZ") == pytest.approx(1 - lam, abs=1e-15)
+            assert D.expect_pauli(rho, "YY") == pytest.approx(-(1 - lam), abs=1e-15)
+
+
+def test_bell_amplitude_damping():
+    for g in (0.0, 0.05, 0.3, 1.0):
+        rho = D.amplitude_damp(_bell(), 0, g)
+        expect = np.zeros((4, 4), dtype=np.complex128)
+        expect[0, 0] = 0.5
+        expect[2, 2] = g / 2
+        expect[3, 3] = (1 - g) / 2
+        expect[0, 3] = expect[3, 0] = np.sqrt(1 - g) / 2
+        assert np.max(np.abs(rho - expect)) < 1e-16
+
+
+def test_ghz_depolarized():
+    n = 5
+    N = 1 << n
+    v = np.zeros(N, dtype=np.complex128)
+    v[0] = v[-1] = 1 / np.sqrt(2)
+    ghz = np.outer(v, v.conj())
+    p = 0.12
+    lam = 4 * p / 3
+    for q in range(n):
+        rho = D.depolarize(ghz, q, p)
+        assert rho[0, 0].real == pytest.approx(0.5 - lam / 4, abs=1e-15)
+        assert rho[N - 1, N - 1].real == pytest.approx(0.5 - lam / 4, abs=1e-15)
+        assert rho[1 << q, 1 << q].real == pytest.approx(lam / 4, abs=1e-15)
+        assert rho[(N - 1) ^ (1 << q), (N - 1) ^ (1 << q)].real == pytest.approx(lam / 4, abs=1e-15)
+        assert rho[0, N - 1].real == pytest.approx((1 - lam) / 2, abs=1e-15)
+        others = np.abs(rho).copy()
+        for (i, j) in [(0, 0), (N - 1, N - 1), (1 << q, 1 << q),
+                       ((N - 1) ^ (1 << q), (N - 1) ^ (1 << q)), (0, N - 1), (N - 1, 0)]:
+            others[i, j] = 0
+        assert others.max() < 1e-16
+
+
+def test_dephasing_closed_form():
+    """Dephasing p multiplies every coherence across qubit q by (1 - 2p)."""
+    rng = S.rng_for(13)
+    n = 3
+    rho = S.ginibre_state(rng, 1 << n)
+    for q in range(n):
+        got = D.dephase(rho, q, 0.2)
+        N = 1 << n
+        fac = np.array([[1.0 if ((i ^ j) >> q) & 1 == 0 else 0.6 for j in range(N)] for i in range(N)])
+        assert np.max(np.abs(got - rho * fac)) < 1e-15
+
+
+# ---------------------------------------------------------------- invariants
+def test_invariants_on_random_circuits():
+    for seed in range(3):
+        rng = S.rng_for(100 + seed)
+        n = 4
+        rho = S.ginibre_state(rng, 1 << n)
+        ops = S.random_mixed_circuit(rng, n, 40)
+        for op in ops:
+            before = rho
+            rho, _ = D.apply_op(rho, op)
+            assert np.max(np.abs(rho - rho.conj().T)) < 1e-14
+            assert abs(np.trace(rho) - 1) < 1e-13
+            ev = np.linalg.eigvalsh(0.5 * (rho + rho.conj().T))
+            assert ev.min() > -1e-13
+            if op["kind"] == "unitary":
+                e0 = np.linalg.eigvalsh(0.5 * (before + before.conj().T))
+                assert np.max(np.abs(ev - e0)) < 1e-13
+
+
+def test_trace_duality():
+    """tr(O Phi(rho)) = tr(Phi*(O) rho) for a 20-op circuit (Sec. I, Sec. II)."""
+    for seed in range(3):
+        rng = S.rng_for(200 + seed)
+        n = 4
+        rho = S.ginibre_state(rng, 1 << n)
+        strings, coeffs = S.random_pauli_sum(rng, n, 16)
+        O = D.pauli_sum(strings, coeffs)
+        ops = S.random_mixed_circuit(rng, n, 20, with_measure=False)
+        rho_t, _ = D.run_circuit(rho, ops, "schrodinger")
+        O_t, _ = D.run_circuit(O, list(reversed(ops)), "heisenberg")
+        assert D.expect(rho_t, O) == pytest.approx(D.expect(rho, O_t), abs=1e-12)
+
+
+def test_heisenberg_of_hadamard():
+    Hd = np.array([[1, 1], [1, -1]], dtype=np.complex128) / np.sqrt(2)
+    assert np.max(np.abs(D.apply_unitary(D.Z, Hd, [0], "heisenberg") - D.X)) < 1e-15
+    # Heisenberg of amplitude damping on Z: K0^+ Z K0 + K1^+ Z K1 = diag(1, 1-2g)... = (g) I + (1-g) Z
+    g = 0.3
+    got = D.amplitude_damp(D.Z, 0, g, "heisenberg")
+    assert np.max(np.abs(got - (g * np.eye(2) + (1 - g) * D.Z))) < 1e-15
+
+
+# ---------------------------------------------------------------- measurement
+def test_measurement_probabilities_and_repeat():
+    rng = S.rng_for(300)
+    n = 4
+    rho = S.ginibre_state(rng, 1 << n)
+    for q in range(n):
+        p0, p1 = D.born_probabilities(rho, q)
+        assert p0 + p1 == pytest.approx(np.trace(rho).real, abs=1e-14)
+        diag = np.real(np.diag(rho))
+        assert p0 == pytest.approx(sum(diag[i] for i in range(1 << n) if not (i >> q) & 1), abs=1e-15)
+        for u in (0.1, 0.9):
+            post, b, pb = D.measure(rho, q, u)
+            assert b == (0 if u < p0 else 1)
+            assert np.trace(post).real == pytest.approx(1.0, abs=1e-14)
+            again, b2, pb2 = D.measure(post, q, 0.5)
+            assert b2 == b and pb2 == pytest.approx(1.0, abs=1e-14)
+            for i in range(1 << n):
+                for j in range(1 << n):
+                    if ((i >> q) & 1) != b or ((j >> q) & 1) != b:
+                        assert post[i, j] == 0
+
+
+# ---------------------------------------------------------------- readouts
+def test_pauli_expectations_on_basis_and_ghz():
+    n = 4
+    for x in range(1 << n):
+        rho = np.zeros((1 << n, 1 << n), dtype=np.complex128)
+        rho[x, x] = 1
+        for l in range(n):
+            s = ["I"] * n
+            s[l] = "Z"
+            assert D.expect_pauli(rho, "".join(s)) == (-1) ** ((x >> l) & 1)
+            s[l] = "X"
+            assert D.expect_pauli(rho, "".join(s)) == 0
+    v = np.zeros(1 << n, dtype=np.complex128)
+    v[0] = v[-1] = 1 / np.sqrt(2)
+    ghz = np.outer(v, v.conj())
+    assert D.expect_pauli(ghz, "X" * n) == pytest.approx(1.0)
+    assert D.expect_pauli(ghz, "ZZII") == pytest.approx(1.0)
+    assert D.expect_pauli(_bell(), "YY") == pytest.approx(-1.0)
+    assert D.expect_pauli(np.eye(1 << n) / (1 << n), "XYZI") == 0
+
+
+def test_tiled_mean_value_equals_trace():
+    rng = S.rng_for(400)
+    for n, m in ((3, 1), (5, 2), (6, 5), (2, 5), (6, 3)):
+        rho = S.ginibre_state(rng, 1 << n)
+        O = S.random_hermitian(rng, 1 << n)
+        got = T.tiled_mean_value(T.to_tiled(rho, m), T.to_tiled(O, m), n, m)
+        assert got == pytest.approx(np.trace(rho @ O).real, abs=1e-13)
+
+
+def test_trace_distance_closed_form():
+    a = np.diag([1.0, 0.0]).astype(np.complex128)
+    b = np.diag([0.0, 1.0]).astype(np.complex128)
+    assert D.trace_distance(a, b) == pytest.approx(1.0)
+    assert D.trace_distance(a, 0.5 * np.eye(2)) == pytest.approx(0.5)
+
+
+# ---------------------------------------------------------------- teeth
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Plant typical oracle mistakes on the CPU and check a pin fails."""
+    # 1) a dropped conjugate: K H K^T instead of K H K^dagger
+    def bad_conj(K, H):
+        KH = D._left(K, H)
+        return D._left(K, KH.T).T
+    with monkeypatch.context() as mp:
+        mp.setattr(D, "_conjugate", bad_conj)
+        with pytest.raises(AssertionError):
+            test_bell_depolarized_is_werner()
+    # 2) a dropped Kraus term
+    orig = D.depolarizing_kraus
+    with monkeypatch.context() as mp:
+        mp.setattr(D, "depolarizing_kraus", lambda p: orig(p)[:3])
+        with pytest.raises(AssertionError):
+            test_depolarizing_closed_form()
+    # 3) a transposed operator in the embedding
+    orig_embed = D.embed
+    with monkeypatch.context() as mp:
+        mp.setattr(D, "embed", lambda L, q, n, sparse=None: orig_embed(np.asarray(L).T, q, n, sparse))
+        with pytest.raises(AssertionError):
+            test_cnot_on_basis_states()
+    # 4) a wrong sign in Y
+    with monkeypatch.context() as mp:
+        mp.setattr(D, "PAULI", dict(D.PAULI, Y=-D.Y))
+        with pytest.raises(AssertionError):
+            test_bell_depolarized_is_werner()
+    # 5) swapped qubit order in the Kronecker product
+    with monkeypatch.context() as mp:
+        mp.setattr(D, "embed", lambda L, q, n, sparse=None: orig_embed(L, [n - 1 - x for x in q], n, sparse))
+        with pytest.raises(AssertionError):
+            test_bell_amplitude_damping()
