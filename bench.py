@@ -1,0 +1,430 @@
+#!/usr/bin/env python
+"""k-local ops/s of the Orkan hot path on GB300 (one JSON line on stdout).
+
+Workload (the per-op sweep at full size): an n = 14 operator in the tiled
+lower-triangle layout (m = 5, 2.15 GB per operand at 16 B/element).  One step
+is one pass of the whole hot path:
+
+  Schroedinger, on a mixed state rho (Haar pure state depolarised on every
+  qubit): for every target q a Haar 1-qubit U, depolarising p = 0.1 (4 Kraus),
+  amplitude damping gamma = 0.05 (2 Kraus), a Haar 2-qubit U on (q, q+1) and
+  on (q, n-1-q); then a Z measurement with a seeded draw, 8 Pauli-string
+  expectations and the trace;
+  Heisenberg, on a 16-term Pauli-sum observable O: the adjoint sweep in
+  reverse order, then tr(rho O) from the tiled Frobenius products.
+
+value = k-local ops (2 x 70 + 1 measurement per step) / device time, with the
+operands resident in HBM and continuously evolved (as in Sec. IV-A).  e2e
+repeats the step through the same C ABI with the operands uploaded from
+pinned host memory every step and the scalars read back.  Under torchrun each
+rank runs an independent replica (weak scaling, no collective on the data
+path); value sums ops over ranks and divides by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "k-local ops/s & HBM % peak, plain FP64 vs served/batched/FP32 forms; p50/p99"
+UNIT = "ops/s"
+DTYPE_NAMES = {"c128": 0, "c64": 1, "df64": 2}
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["orkan", "reference"], default="orkan")
+    p.add_argument("--dtype", choices=list(DTYPE_NAMES), default="df64")
+    p.add_argument("--n", type=int, default=14)
+    p.add_argument("--tile-log2", type=int, default=5)
+    p.add_argument("--fusion", type=int, default=8)
+    p.add_argument("--no-compose", action="store_true")
+    p.add_argument("--no-variants", action="store_true", help="skip the c128 / c64 / unfused comparison runs")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=20.0)
+    return p.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(units: float, seconds: float, group=None):
+    """Whole-job throughput: sum of units over ranks / max of seconds over ranks."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return units, seconds
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" else torch.device("cpu")
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    s = torch.tensor([float(seconds)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX, group=group)
+    return float(u.item()), float(s.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        loaded = sorted(sm)[len(sm) // 2:] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workload
+def make_workload(n: int):
+    from workloads import synth as S
+    rng = S.rng_for(S.BASE_SEED + 1)
+    ops = S.sweep(n)
+    psi = S.haar_state_vector(rng, 1 << n)
+    paulis = S.random_pauli_strings(rng, n, 8)
+    obs_strings, obs_coeffs = S.random_pauli_sum(rng, n, 16)
+    us = rng.uniform(0.0, 1.0, 64)
+    return {"ops": ops, "psi": psi, "paulis": paulis, "obs": (obs_strings, obs_coeffs), "us": us}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_record(dtype: str):
+    """DRAM bytes per pass-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "pass_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_2604_15765_gb300", "csrc", "pass_kernels.cu")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        ent = rec.get(dtype)
+        if ent and ent.get("source_sha256_16") == digest:
+            return ent
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+class Runner:
+    """Two handles (rho, O) on one stream, the sweep issued through the C ABI."""
+
+    def __init__(self, ok, circuit, wl, n, m, dtype, fusion, compose, stream):
+        self.ok, self.circuit, self.wl = ok, circuit, wl
+        self.n = n
+        self.rho = ok.orkan_alloc(n, DTYPE_NAMES[dtype], m)
+        self.O = ok.orkan_alloc(n, DTYPE_NAMES[dtype], m)
+        for h in (self.rho, self.O):
+            ok.orkan_set_stream(h, stream)
+            ok.orkan_set_fusion(h, fusion, compose)
+        ok.orkan_init_state(self.rho, ok.ORKAN_INIT_PURE, wl["psi"])
+        for q in range(n):
+            ok.orkan_depolarize(self.rho, q, 0.1)
+        ok.orkan_init_observable(self.O, *wl["obs"])
+        ok.orkan_sync(self.rho)
+        self.bytes = ok.orkan_bytes(n, DTYPE_NAMES[dtype], m)
+        self.step_idx = 0
+        self.ops_per_step = 2 * len(wl["ops"]) + 1
+
+    def step(self):
+        ok, c, wl = self.ok, self.circuit, self.wl
+        for op in wl["ops"]:
+            c.apply_op(self.rho, op, "schrodinger")
+        q = self.step_idx % self.n
+        u = float(wl["us"][self.step_idx % len(wl["us"])])
+        res = [ok.orkan_measure(self.rho, q, u)[1]]
+        res += [ok.orkan_expect_pauli(self.rho, s) for s in wl["paulis"]]
+        res.append(ok.orkan_trace(self.rho).real)
+        for op in reversed(wl["ops"]):
+            c.apply_op(self.O, op, "heisenberg")
+        res.append(ok.orkan_expect(self.rho, self.O))
+        self.step_idx += 1
+        return res
+
+    def launches(self):
+        return sum(self.ok.orkan_stats(h)["launches"] for h in (self.rho, self.O))
+
+    def timing(self, enable):
+        for h in (self.rho, self.O):
+            self.ok.orkan_set_timing(h, enable)
+
+    def pass_time(self):
+        ms, cnt = 0.0, 0
+        for h in (self.rho, self.O):
+            a, b = self.ok.orkan_pass_time(h)
+            ms += a
+            cnt += b
+        return ms, cnt
+
+    def free(self):
+        self.ok.orkan_free(self.rho)
+        self.ok.orkan_free(self.O)
+
+
+def time_steps(runner, steps, warmup, torch):
+    for _ in range(warmup):
+        runner.step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    l0 = runner.launches()
+    runner.timing(True)
+    runner.pass_time()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        runner.step()
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    pass_ms, pass_cnt = runner.pass_time()
+    runner.timing(False)
+    return ms, pass_ms, pass_cnt, runner.launches() - l0
+
+
+def cpu_baseline(wl, n, seconds):
+    """The oracle as it stands, on the same sweep at the same n, until the time
+    budget is spent (at least one op); returns ops/s and the sample."""
+    import numpy as np
+    from oracle import dense as D
+    psi = wl["psi"]
+    rho = np.outer(psi, psi.conj())
+    t0 = time.perf_counter()
+    done = 0
+    for op in wl["ops"]:
+        rho, _ = D.apply_op(rho, op)
+        done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {done} ops of the n={n} sweep on a dense complex128 rho (scipy.sparse Kronecker "
+                      f"K, single-threaded), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle, timed as it stands on the host cores."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import dense as D
+    wl = make_workload(args.n)
+    ops = wl["ops"]
+    psi = wl["psi"]
+    rho = np.outer(psi, psi.conj())
+    k = 0
+    for _ in range(args.warmup):
+        rho, _ = D.apply_op(rho, ops[k % len(ops)])
+        k += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rho, _ = D.apply_op(rho, ops[k % len(ops)])
+        k += 1
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": f"per-op sweep n={args.n} (one k-local op of the sweep per step)", "n": args.n},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} ops of the n={args.n} sweep, one per step, dense complex128 oracle"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2604_15765_gb300 import build as _b
+    _b.build()
+    from paper_2604_15765_gb300 import circuit
+    from paper_2604_15765_gb300 import orkan as ok
+
+    n, m = args.n, args.tile_log2
+    wl = make_workload(n)
+    stream = torch.cuda.current_stream().cuda_stream
+    compose = not args.no_compose
+    runner = Runner(ok, circuit, wl, n, m, args.dtype, args.fusion, compose, stream)
+
+    # ---- device-resident throughput
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:
+        gpu_id = str(local)
+    with ClockSampler(gpu_id) as clk:
+        ms, pass_ms, pass_cnt, launches = time_steps(runner, args.steps, args.warmup, torch)
+    clocks = clk.summary()
+    units = runner.ops_per_step * args.steps
+    tot_units, tot_s = aggregate(units, ms / 1e3)
+    value = tot_units / tot_s
+
+    # ---- end to end through the C ABI from pinned host buffers
+    host_rho = torch.empty(runner.bytes, dtype=torch.uint8, pin_memory=True)
+    host_O = torch.empty(runner.bytes, dtype=torch.uint8, pin_memory=True)
+    ok.orkan_store_tiled(runner.rho, host_rho.numpy())
+    ok.orkan_store_tiled(runner.O, host_O.numpy())
+    e2e_steps = max(2, args.steps // 2)
+
+    def e2e_step():
+        ok.orkan_load_tiled(runner.rho, host_rho.numpy(), ok.ORKAN_STATE)
+        ok.orkan_load_tiled(runner.O, host_O.numpy(), ok.ORKAN_OBSERVABLE)
+        return runner.step()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_units, e2e_tot = aggregate(runner.ops_per_step * e2e_steps, e2e_s)
+    op_bytes = sum(16 * op["matrix"].size if op["kind"] == "unitary" else 8 for op in wl["ops"]) * 2
+    h2d = 2 * runner.bytes + op_bytes
+    d2h = 8 * (1 + len(wl["paulis"]) + 2 + 1) + 8
+
+    # ---- roofline of the dominant kernel (the fused pass kernel)
+    hbm_peak, peak_kind = peaks()
+    avg_pass_ms = pass_ms / max(pass_cnt, 1)
+    achieved = 2.0 * runner.bytes / (avg_pass_ms * 1e-3) / 1e9
+    trec = traffic_record(args.dtype)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": (trec or {}).get("bytes_per_launch"),
+                "kernel": "pass_kernel (fused tile-group conjugation)", "peak_kind": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": 2 * runner.bytes, "avg_launch_ms": round(avg_pass_ms, 4),
+                "launches": pass_cnt, "pass_share_of_step": round(pass_ms / ms, 4) if ms > 0 else None}
+    runner.free()
+
+    # ---- comparison runs (rank 0 only): plain FP64 one-op-per-pass, fused c128, c64
+    variants = {}
+    if not args.no_variants and world == 1:
+        for name, dt, fus, comp in (("c128_plain_unfused", "c128", 1, False), ("c128_fused", "c128", args.fusion, True),
+                                    ("df64_unfused", "df64", 1, False), ("c64_fused", "c64", args.fusion, True)):
+            if dt == args.dtype and fus == args.fusion and comp == compose:
+                continue
+            r = Runner(ok, circuit, wl, n, m, dt, fus, comp, stream)
+            vms, vpass, vcnt, _ = time_steps(r, max(2, args.steps // 3), 1, torch)
+            variants[name] = {"value": round(r.ops_per_step * max(2, args.steps // 3) / (vms / 1e3), 1), "unit": UNIT,
+                              "avg_pass_GBps": round(2.0 * r.bytes / (vpass / max(vcnt, 1) * 1e-3) / 1e9, 1)}
+            r.free()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, n, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(tot_s * 1e3 / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": f"per-op sweep n={n}, tiled m={m}: every target, 1q Haar U + depolarising p=0.1 "
+                                   f"+ amplitude damping 0.05 + 2q Haar U adjacent and far; Schroedinger + "
+                                   f"Heisenberg; Z measurement, 8 Pauli expectations, trace, tr(rho O)",
+                       "n": n, "tile_log2": m, "fusion": args.fusion, "compose": compose,
+                       "ops_per_step": runner.ops_per_step, "state_bytes": runner.bytes,
+                       "l2": "no flush: each operand (%.2f GB) is larger than the 129 MB L2" % (runner.bytes / 1e9),
+                       "parallelism": f"replicas{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_units / e2e_tot, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

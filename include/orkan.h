@@ -1,0 +1,230 @@
+/*
+ * orkan.h -- C ABI of the Orkan GB300 library: single-pass k-local conjugation
+ * of a hermitian operator stored in the tiled lower-triangle layout.
+ *
+ * The method (arXiv:2604.15765, "Orkan: Cache-friendly simulation of quantum
+ * operations on hermitian operators"):
+ *   - Eq. (1), Sec. II: a quantum operation in Kraus form,
+ *       Phi(H) = sum_alpha K_alpha H K_alpha^dagger,
+ *     acting on any hermitian H (a density matrix or an observable).
+ *   - Sec. I / Sec. II: the Heisenberg picture applies the trace-dual map
+ *       Phi*(O) = sum_alpha K_alpha^dagger O K_alpha.
+ *   - Sec. II-A, Eq. (2): a k-local operation K = I (x) L updates every
+ *     2^k x 2^k block h_{s,s'} independently: h -> sum L h L^dagger.
+ *   - Sec. III-B: storage keeps the lower triangle at tile granularity
+ *     (tiles of edge M = 2^m, tile (ti, tj) with ti >= tj, tiles row-major,
+ *     elements row-major in a tile, diagonal tiles complete, zero padding to
+ *     one M x M tile if N < M).  N (N + M) / 2 elements (Table I).
+ *   - Sec. III-C: the mean value tr(rho O) as per-tile Frobenius products.
+ *
+ * Conventions
+ *   - Qubit a is bit a of a basis index (qubit 0 = least significant bit).
+ *   - A 2^k x 2^k matrix L given with qubits[0..k-1] maps bit l of its own
+ *     row/column index to qubit qubits[l].  Matrices are row-major,
+ *     complex128 interleaved (re, im), i.e. 2 * 4^k doubles.
+ *   - Handles are stream-ordered: every call enqueues work on the handle's
+ *     CUDA stream and returns; calls that return scalars or host data wait
+ *     for the stream.  Consecutive operations are fused into one pass over
+ *     the state when their qubits allow it (see orkan_set_fusion).
+ *   - Input matrices and strings are copied during the call; the caller
+ *     keeps ownership of every pointer it passes.
+ *   - A handle is used from one host thread at a time.
+ *
+ * Status codes: ORKAN_OK (0) or a negative ORKAN_E* value; no C++ exception
+ * ever crosses this boundary.  orkan_strerror() names a code and
+ * orkan_last_error() returns a message for the calling thread's last error.
+ */
+#ifndef ORKAN_H
+#define ORKAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORKAN_OK 0
+#define ORKAN_EINVAL (-1)    /* bad argument: qubit out of range or repeated, k > 2, r > 4^k, ... */
+#define ORKAN_ENOMEM (-2)    /* device or host allocation failed */
+#define ORKAN_ECUDA (-3)     /* a CUDA call failed (message in orkan_last_error) */
+#define ORKAN_EZEROPROB (-4) /* measurement: the selected outcome has probability < 1e-300 */
+#define ORKAN_EPICTURE (-5)  /* operation not defined in the handle's picture */
+#define ORKAN_ENODEV (-6)    /* no CUDA device */
+
+/* Storage dtype.
+ *   ORKAN_C128: complex128 elements, native FP64 arithmetic (16 B/element).
+ *   ORKAN_C64 : complex64 elements, FP32 arithmetic (8 B/element).
+ *   ORKAN_DF64: "double-float" elements -- real and imaginary part each kept
+ *               as an unevaluated sum hi + lo of two floats (16 B/element) --
+ *               with FP32-pipe error-free arithmetic, about 48 significand
+ *               bits.  Values must stay within the float exponent range
+ *               (|x| < 3e38; parts below 1e-38 flush to zero).
+ * Readouts (trace, probabilities, expectations) accumulate in FP64 for all. */
+#define ORKAN_C128 0
+#define ORKAN_C64 1
+#define ORKAN_DF64 2
+
+/* Picture of a handle, set by orkan_init_state / orkan_init_observable. */
+#define ORKAN_STATE 0
+#define ORKAN_OBSERVABLE 1
+
+/* orkan_init_state kinds. */
+#define ORKAN_INIT_ZERO 0     /* |0...0><0...0|, data ignored */
+#define ORKAN_INIT_MAXMIXED 1 /* I / N, data ignored */
+#define ORKAN_INIT_DENSE 2    /* data: N x N complex128 row-major (2 N^2 doubles); lower triangle is read */
+#define ORKAN_INIT_PURE 3     /* data: N complex128 amplitudes psi (2 N doubles); rho = psi psi^dagger */
+
+typedef struct orkan_ctx *orkan_h;
+
+/* ------------------------------------------------------------------ errors */
+const char *orkan_strerror(int status);
+/* Message of the calling thread's most recent failing call ("" if none). */
+const char *orkan_last_error(void);
+
+/* ------------------------------------------------------------------ layout (host only, no GPU needed)
+ * Sec. III-B and Table I. */
+
+/* Bytes of the tiled array: N (N + M) / 2 elements, or M^2 if N < M, times the
+ * element size (16 for C128 and DF64, 8 for C64).  0 on bad arguments. */
+size_t orkan_bytes(int n, int dtype, int tile_log2);
+
+/* Number of stored tiles Nt (Nt + 1) / 2 with Nt = max(1, N / M); -1 on bad arguments. */
+int64_t orkan_num_tiles(int n, int tile_log2);
+
+/* Element offset of H[i, j] in the tiled array; *conj is set to 1 when the
+ * stored value is the conjugate of H[i, j] (i < j), else 0.  -1 if out of range. */
+int64_t orkan_element_offset(int n, int tile_log2, int64_t i, int64_t j, int *conj);
+
+/* Subroutine 1 (insertBits): the global index whose bits at the ascending
+ * positions pos[0..k-1] are the bits of a (bit l at pos[l]) and whose other
+ * bits, in order, are the bits of s. */
+uint64_t orkan_insert_bits(uint64_t s, uint64_t a, int k, const int *pos);
+
+/* Pauli transfer matrix of the k-local map with r Kraus operators K (r
+ * matrices of 2^k x 2^k, layout as above), in FP64 on the host:
+ *   R[a][b] = 2^-k tr(P_a Phi(P_b)), P_a = sigma_{a_{k-1}} (x) ... (x) sigma_{a_0},
+ * a = a_0 + 4 a_1 (sigma_0..3 = I, X, Y, Z).  adjoint != 0 gives the map
+ * Phi* instead.  out: 16^k doubles, row-major.  This is the representation
+ * the kernels apply for single-qubit maps (the transfer matrix of Eq. (3) in
+ * the Pauli basis, where it is real). */
+int orkan_ptm(int k, int r, const double *K, int adjoint, double *out);
+
+/* ------------------------------------------------------------------ lifetime */
+
+/* Allocate an n-qubit operator (1 <= n <= 24) with tile edge 2^tile_log2
+ * (2 <= tile_log2 <= 5; the paper's m = 5 is the default when tile_log2 is 0)
+ * on the current CUDA device.  The content is undefined until an init call.
+ * Errors: EINVAL, ENOMEM, ENODEV, ECUDA. */
+int orkan_alloc(int n, int dtype, int tile_log2, orkan_h *out);
+
+/* Same, on caller-owned device memory of at least orkan_bytes(...) bytes,
+ * 256-byte aligned (e.g. a torch tensor); orkan_free does not release it. */
+int orkan_alloc_external(int n, int dtype, int tile_log2, void *dev_ptr, size_t bytes, orkan_h *out);
+
+/* Wait for the handle's work and release it (and its memory unless external). */
+int orkan_free(orkan_h h);
+
+/* Run the handle's work on the given cudaStream_t (NULL = the legacy default
+ * stream).  Pending fused ops are flushed on the old stream first. */
+int orkan_set_stream(orkan_h h, void *cuda_stream);
+
+/* Fusion policy: at most max_ops (1..16) consecutive ops per pass; compose
+ * != 0 lets consecutive single-qubit ops on the same qubit be multiplied
+ * into one transfer matrix in FP64 on the host.  Default: 8, 1.
+ * max_ops = 1 with compose = 0 is the plain one-pass-per-op path. */
+int orkan_set_fusion(orkan_h h, int max_ops, int compose);
+
+int orkan_get_info(orkan_h h, int *n, int *dtype, int *tile_log2, int *picture);
+
+/* Device address of the tiled array (layout of Sec. III-B, element type of the dtype). */
+void *orkan_device_ptr(orkan_h h);
+
+/* ------------------------------------------------------------------ initialisation */
+
+/* Set the handle to a state (picture ORKAN_STATE).  See ORKAN_INIT_*.
+ * Errors: EINVAL (unknown kind, NULL data for DENSE/PURE), ENOMEM, ECUDA. */
+int orkan_init_state(orkan_h h, int kind, const double *data);
+
+/* Set the handle to the observable O = sum_t coeffs[t] P_t (picture
+ * ORKAN_OBSERVABLE).  paulis: nterms strings of n characters from "IXYZ"
+ * back to back (no separators); character l acts on qubit l.
+ * Errors: EINVAL (bad character, nterms < 0), ENOMEM, ECUDA. */
+int orkan_init_observable(orkan_h h, int nterms, const char *paulis, const double *coeffs);
+
+/* Raw tiled array copies (checkpoint / resume): host_src / host_dst hold
+ * orkan_bytes(...) bytes in the handle's dtype and layout. */
+int orkan_load_tiled(orkan_h h, const void *host_src, int picture);
+int orkan_store_tiled(orkan_h h, void *host_dst);
+
+/* ------------------------------------------------------------------ operations
+ * On a STATE handle these apply Phi (Eq. 1); on an OBSERVABLE handle Phi*
+ * (the caller issues a circuit's ops in reverse order for Heisenberg
+ * evolution). */
+
+/* Unitary gate U (2^k x 2^k, k = 1 or 2) on qubits[0..k-1] (distinct, < n). */
+int orkan_apply_unitary(orkan_h h, int k, const int *qubits, const double *U);
+
+/* Kraus map with r (1 <= r <= 4^k) operators K (r matrices back to back) on
+ * k = 1 or 2 qubits.  Trace non-increase is not checked. */
+int orkan_apply_kraus(orkan_h h, int k, const int *qubits, int r, const double *K);
+
+/* Depolarising channel of Sec. IV-A: Kraus sqrt(1-p) I, sqrt(p/3) {X, Y, Z}. */
+int orkan_depolarize(orkan_h h, int q, double p);
+/* Dephasing (phase flip): sqrt(1-p) I, sqrt(p) Z.  Not defined in the paper. */
+int orkan_dephase(orkan_h h, int q, double p);
+/* Amplitude damping: diag(1, sqrt(1-gamma)), sqrt(gamma)|0><1|.  Not defined in the paper. */
+int orkan_amplitude_damp(orkan_h h, int q, double gamma);
+
+/* Z-basis measurement of qubit q on a STATE handle with the caller's uniform
+ * draw u in [0, 1): p_b = tr(Pi_b rho) in FP64, outcome = 0 iff
+ * u (p0 + p1) < p0, then rho <- Pi_b rho Pi_b / p_b (Born renormalisation).
+ * *outcome and *prob (= p_b / (p0 + p1)) are written on success.
+ * Blocks until the probabilities are known.
+ * Errors: EPICTURE on an observable, EZEROPROB, EINVAL. */
+int orkan_measure(orkan_h h, int q, double u, int *outcome, double *prob);
+
+/* Pi_b H Pi_b without renormalisation (both pictures). */
+int orkan_project(orkan_h h, int q, int outcome);
+
+/* ------------------------------------------------------------------ readouts (block; FP64) */
+
+/* tr H = sum_i H_ii (re, im). */
+int orkan_trace(orkan_h h, double *re, double *im);
+
+/* tr(P H) for the Pauli string P (n characters of "IXYZ", character l on qubit l). */
+int orkan_expect_pauli(orkan_h h, const char *pauli, double *out);
+
+/* tr(rho O) as tiled Frobenius products (Sec. III-C; diagonal tiles once,
+ * strictly lower tiles twice).  Both handles: same n, tile size and dtype. */
+int orkan_expect(orkan_h rho, orkan_h O, double *out);
+
+/* Dense N x N complex128 row-major copy into host memory out (2 N^2 doubles).
+ * Elements above the diagonal are conjugates of the stored lower ones. */
+int orkan_to_dense(orkan_h h, double *out);
+
+/* Gather count elements H[rows[t], cols[t]] (any triangle; upper ones are
+ * conjugated stored values) into host memory out (2 count doubles, complex128).
+ * rows / cols: host arrays of count indices in [0, N).  Errors: EINVAL. */
+int orkan_get_elements(orkan_h h, int64_t count, const int64_t *rows, const int64_t *cols, double *out);
+
+/* Launch any pending fused ops / wait for the handle's stream. */
+int orkan_flush(orkan_h h);
+int orkan_sync(orkan_h h);
+
+/* ------------------------------------------------------------------ instrumentation */
+
+/* Counters since allocation: passes launched, ops applied, kernels launched. */
+int orkan_stats(orkan_h h, int64_t *passes, int64_t *ops, int64_t *launches);
+
+/* enable != 0: bracket every pass launch with CUDA events on the handle's stream. */
+int orkan_set_timing(orkan_h h, int enable);
+
+/* Wait for the stream, then return the summed event time (ms) of the passes
+ * recorded since the last call, their count, and reset. */
+int orkan_pass_time(orkan_h h, double *ms, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ORKAN_H */

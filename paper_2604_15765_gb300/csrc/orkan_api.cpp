@@ -1,0 +1,966 @@
+// Host side of the Orkan GB300 library: the C ABI of include/orkan.h, the
+// FP64 preparation of every op (Pauli transfer matrices, Sec. II-A Eq. 3),
+// and the planner that fuses consecutive ops into passes.
+//
+// An op on qubits A is classified by its high qubits A>=m (Sec. III-C: the
+// number of tiles a k-local update spans grows as 2^(2 |A>=m|)).  Consecutive
+// ops are fused while the union of their high qubits has at most two
+// elements and the tile group still fits the shared-memory budget; a pass is
+// then one read and one write of the tiled array.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/orkan.h"
+#include "orkan_internal.h"
+
+using cd = std::complex<double>;
+using namespace orkan;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(ORKAN_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define ORKAN_CUDA(call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+  } while (0)
+
+int elem_size(int dtype) { return dtype == DT_C64 ? 8 : 16; }
+bool valid_dtype(int dtype) { return dtype == DT_C128 || dtype == DT_C64 || dtype == DT_DF64; }
+
+// ------------------------------------------------------------------ Pauli algebra (FP64)
+const cd kPauli[4][4] = {
+    {1, 0, 0, 1},                                  // I
+    {0, 1, 1, 0},                                  // X
+    {0, cd(0, -1), cd(0, 1), 0},                   // Y
+    {1, 0, 0, -1},                                 // Z
+};
+
+// d x d complex matrices, row-major.
+using Mat = std::vector<cd>;
+
+Mat matmul(const Mat& A, const Mat& B, int d) {
+  Mat C(d * d, 0.0);
+  for (int i = 0; i < d; ++i)
+    for (int k = 0; k < d; ++k) {
+      const cd a = A[i * d + k];
+      if (a == 0.0) continue;
+      for (int j = 0; j < d; ++j) C[i * d + j] += a * B[k * d + j];
+    }
+  return C;
+}
+Mat dagger(const Mat& A, int d) {
+  Mat B(d * d);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) B[j * d + i] = std::conj(A[i * d + j]);
+  return B;
+}
+Mat pauli_string(int a, int k) {
+  // P_a = sigma_{a_{k-1}} (x) ... (x) sigma_{a_0}
+  Mat P{1.0};
+  int dim = 1;
+  for (int l = k - 1; l >= 0; --l) {
+    const int s = (a >> (2 * l)) & 3;
+    Mat Q(dim * 2 * dim * 2);
+    for (int i = 0; i < dim; ++i)
+      for (int j = 0; j < dim; ++j)
+        for (int x = 0; x < 2; ++x)
+          for (int y = 0; y < 2; ++y)
+            Q[(2 * i + x) * (2 * dim) + (2 * j + y)] = P[i * dim + j] * kPauli[s][2 * x + y];
+    P.swap(Q);
+    dim *= 2;
+  }
+  return P;
+}
+
+// Pauli transfer matrix R[a][b] = 2^-k Re tr(P_a Phi(P_b)) of the Kraus set.
+std::vector<double> ptm(int k, const std::vector<Mat>& kraus, bool adjoint) {
+  const int d = 1 << k, np = 1 << (2 * k);
+  std::vector<Mat> P(np);
+  for (int a = 0; a < np; ++a) P[a] = pauli_string(a, k);
+  std::vector<double> R(np * np, 0.0);
+  for (int b = 0; b < np; ++b) {
+    Mat img(d * d, 0.0);
+    for (const Mat& K : kraus) {
+      const Mat Kd = dagger(K, d);
+      const Mat t = adjoint ? matmul(matmul(Kd, P[b], d), K, d) : matmul(matmul(K, P[b], d), Kd, d);
+      for (int i = 0; i < d * d; ++i) img[i] += t[i];
+    }
+    for (int a = 0; a < np; ++a) {
+      const Mat pa = matmul(P[a], img, d);
+      cd tr = 0.0;
+      for (int i = 0; i < d; ++i) tr += pa[i * d + i];
+      R[a * np + b] = tr.real() / d;
+    }
+  }
+  return R;
+}
+
+Mat read_mat(const double* p, int d) {
+  Mat A(d * d);
+  for (int i = 0; i < d * d; ++i) A[i] = cd(p[2 * i], p[2 * i + 1]);
+  return A;
+}
+// Re-express a two-qubit matrix given on (q0, q1) with q0 > q1 in the ascending order.
+Mat swap_local_bits(const Mat& A) {
+  auto p = [](int i) { return ((i & 1) << 1) | (i >> 1); };
+  Mat B(16);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) B[p(i) * 4 + p(j)] = A[i * 4 + j];
+  return B;
+}
+
+// ------------------------------------------------------------------ planned ops
+struct HostOp {
+  int kind = OP_PTM1;
+  int nq = 1;
+  int q[2] = {0, 0};           // ascending
+  std::vector<double> R;       // single-qubit ops: full 4x4 PTM (for composition)
+  std::vector<double> coef;    // kind-specific FP64 coefficients (2-qubit ops)
+};
+
+std::vector<double> mat4mul(const std::vector<double>& A, const std::vector<double>& B) {
+  std::vector<double> C(16, 0.0);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 4; ++k) s += A[i * 4 + k] * B[k * 4 + j];
+      C[i * 4 + j] = s;
+    }
+  return C;
+}
+
+// Coefficients of a single-qubit op from its transfer matrix R.
+std::vector<double> coef_1q(int kind, const std::vector<double>& R) {
+  std::vector<double> c;
+  if (kind == OP_PTM1_U) {
+    for (int i = 1; i < 4; ++i)
+      for (int j = 1; j < 4; ++j) c.push_back(0.5 * R[i * 4 + j]);
+  } else if (kind == OP_PTM1_AD) {
+    const double R00 = R[0], R03 = R[3], R30 = R[12], R33 = R[15];
+    c = {0.5 * (R00 + R30 + R03 + R33), 0.5 * (R00 + R30 - R03 - R33), 0.5 * (R00 - R30 + R03 - R33),
+         0.5 * (R00 - R30 - R03 + R33), R[5], R[9]};
+  } else {
+    for (int i = 0; i < 16; ++i) c.push_back(0.5 * R[i]);
+  }
+  return c;
+}
+
+bool is_ad_pattern(const std::vector<double>& R) {
+  const int zeros[] = {1, 2, 4, 7, 8, 11, 13, 14};
+  for (int z : zeros)
+    if (R[z] != 0.0) return false;
+  return R[5] == R[10] && R[6] == -R[9];
+}
+bool is_unitary_pattern(const std::vector<double>& R) {
+  return R[0] == 1.0 && R[1] == 0.0 && R[2] == 0.0 && R[3] == 0.0 && R[4] == 0.0 && R[8] == 0.0 && R[12] == 0.0;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ the handle
+struct orkan_ctx {
+  Geometry g{};
+  int dtype = DT_C128;
+  int picture = ORKAN_STATE;
+  int device = 0;
+  size_t bytes = 0;
+  void* d_state = nullptr;
+  bool external = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int fusion = 8;
+  bool compose = true;
+  std::vector<HostOp> pending;
+  double* d_partials = nullptr;
+  double* d_res = nullptr;
+  double* h_res = nullptr;   // pinned
+  int64_t n_passes = 0, n_ops = 0, n_launches = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
+};
+
+namespace {
+
+int rows_log2_for(const orkan_ctx* h, int nh) {
+  // 2^(2 nh) tiles x 2^rl rows x M columns within a 64 KiB shared-memory budget
+  const int64_t budget = 64 * 1024;
+  const int64_t per_row = (int64_t(1) << (2 * nh)) * (int64_t(1) << h->g.m) * elem_size(h->dtype);
+  int rl = 0;
+  while (rl < h->g.m && (per_row << (rl + 1)) <= budget) ++rl;
+  return rl;
+}
+
+struct PassShape {
+  int nh = 0;
+  int high[2] = {0, 0};
+  int max_low = -1;
+};
+
+PassShape shape_of(const orkan_ctx* h, const std::vector<HostOp>& ops, const HostOp* extra) {
+  PassShape s;
+  std::vector<int> high;
+  auto add = [&](const HostOp& op) {
+    for (int l = 0; l < op.nq; ++l) {
+      const int q = op.q[l];
+      if (q >= h->g.m) {
+        if (std::find(high.begin(), high.end(), q) == high.end()) high.push_back(q);
+      } else {
+        s.max_low = std::max(s.max_low, q);
+      }
+    }
+  };
+  for (const auto& op : ops) add(op);
+  if (extra) add(*extra);
+  std::sort(high.begin(), high.end());
+  s.nh = int(high.size());
+  for (int i = 0; i < s.nh && i < 2; ++i) s.high[i] = high[i];
+  return s;
+}
+
+int slots_upper_bound(const HostOp& op) { return op.nq == 1 ? 16 : coef_slots(op.kind); }
+
+bool fits(const orkan_ctx* h, const HostOp& op) {
+  if (h->pending.empty()) return true;
+  if (int(h->pending.size()) >= std::min(h->fusion, kMaxOps)) return false;
+  const PassShape s = shape_of(h, h->pending, &op);
+  if (s.nh > 2) return false;
+  if (s.max_low >= rows_log2_for(h, s.nh)) return false;
+  int slots = slots_upper_bound(op);
+  for (const auto& p : h->pending) slots += slots_upper_bound(p);
+  return slots <= kMaxCoef;
+}
+
+void pack_coef(const orkan_ctx* h, PassDesc& d, int slot, double v) {
+  if (h->dtype == DT_C128) {
+    d.coef[slot] = v;
+  } else if (h->dtype == DT_C64) {
+    float f = (float)v;
+    float pair[2] = {f, 0.0f};
+    std::memcpy(&d.coef[slot], pair, 8);
+  } else {
+    const float hi = (float)v;
+    const float lo = (float)(v - (double)hi);
+    float pair[2] = {hi, lo};
+    std::memcpy(&d.coef[slot], pair, 8);
+  }
+}
+
+int flush_pending(orkan_ctx* h) {
+  if (h->pending.empty()) return ORKAN_OK;
+  const PassShape s = shape_of(h, h->pending, nullptr);
+  const int rl = rows_log2_for(h, s.nh);
+  PassDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.m = h->g.m;
+  d.h = s.nh;
+  for (int i = 0; i < s.nh; ++i) d.hpos[i] = s.high[i] - h->g.m;
+  d.rows_log2 = rl;
+  d.chunks_log2 = h->g.m - rl;
+  d.nt_c = h->g.Nt >> s.nh;
+  // A chunked pass splits tile rows over work items; in a diagonal group the
+  // mirrored slots would then read rows another item is writing, so those
+  // groups go to the full-height diagonal kernel instead.
+  d.skip_diag = d.chunks_log2 > 0 ? 1 : 0;
+  const int64_t groups = d.skip_diag ? d.nt_c * (d.nt_c - 1) / 2 : d.nt_c * (d.nt_c + 1) / 2;
+  d.n_items = groups << d.chunks_log2;
+  int slot = 0;
+  for (const HostOp& op : h->pending) {
+    PassOp& po = d.ops[d.nops++];
+    po.kind = op.kind;
+    po.nq = op.nq;
+    for (int l = 0; l < op.nq; ++l) {
+      const int q = op.q[l];
+      if (q < h->g.m) {
+        po.rbit[l] = q;
+        po.cbit[l] = q;
+      } else {
+        const int p = (q == s.high[0]) ? 0 : 1;
+        po.rbit[l] = rl + p;
+        po.cbit[l] = h->g.m + p;
+      }
+    }
+    po.coef = slot;
+    const std::vector<double> c = op.nq == 1 ? coef_1q(op.kind, op.R) : op.coef;
+    for (double v : c) pack_coef(h, d, slot++, v);
+  }
+  const int64_t nops = int64_t(h->pending.size());
+  h->pending.clear();
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (h->timing) {
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t e;
+      if (!h->ev_free.empty()) {
+        e = h->ev_free.back();
+        h->ev_free.pop_back();
+      } else {
+        ORKAN_CUDA(cudaEventCreate(&e));
+      }
+      (i == 0 ? ev.first : ev.second) = e;
+    }
+    ORKAN_CUDA(cudaEventRecord(ev.first, h->stream));
+  }
+  int nlaunch = 0;
+  ORKAN_CUDA(launch_pass(h->dtype, h->d_state, d, h->stream, &nlaunch));
+  if (h->timing) {
+    ORKAN_CUDA(cudaEventRecord(ev.second, h->stream));
+    h->ev_used.push_back(ev);
+  }
+  h->n_passes += 1;
+  h->n_ops += nops;
+  h->n_launches += nlaunch;
+  return ORKAN_OK;
+}
+
+int enqueue(orkan_ctx* h, HostOp op) {
+  // compose consecutive single-qubit ops on the same qubit (FP64, on the host)
+  if (h->compose && op.nq == 1 && !h->pending.empty()) {
+    HostOp& last = h->pending.back();
+    if (last.nq == 1 && last.q[0] == op.q[0]) {
+      last.R = mat4mul(op.R, last.R);
+      if (!(last.kind == op.kind && (op.kind == OP_PTM1_U || op.kind == OP_PTM1_AD))) {
+        last.kind = is_unitary_pattern(last.R) ? OP_PTM1_U : (is_ad_pattern(last.R) ? OP_PTM1_AD : OP_PTM1);
+      }
+      h->n_ops += 1;
+      return ORKAN_OK;
+    }
+  }
+  if (!fits(h, op)) {
+    const int st = flush_pending(h);
+    if (st != ORKAN_OK) return st;
+  }
+  h->pending.push_back(std::move(op));
+  if (int(h->pending.size()) >= std::min(h->fusion, kMaxOps)) return flush_pending(h);
+  return ORKAN_OK;
+}
+
+int check_handle(orkan_h h) {
+  if (!h) return fail(ORKAN_EINVAL, "null handle");
+  return ORKAN_OK;
+}
+
+int check_qubits(const orkan_ctx* h, int k, const int* qubits) {
+  if (k < 1 || k > 2 || !qubits) return fail(ORKAN_EINVAL, "k must be 1 or 2 with a qubit list");
+  for (int l = 0; l < k; ++l)
+    if (qubits[l] < 0 || qubits[l] >= h->g.n) return fail(ORKAN_EINVAL, "qubit out of range");
+  if (k == 2 && qubits[0] == qubits[1]) return fail(ORKAN_EINVAL, "repeated qubit");
+  return ORKAN_OK;
+}
+
+// Build the planned op for a k-local Kraus set given in the caller's qubit order.
+int make_op(orkan_ctx* h, int k, const int* qubits, const std::vector<Mat>& kraus_in, bool unitary, HostOp* out) {
+  const bool adj = (h->picture == ORKAN_OBSERVABLE);
+  HostOp op;
+  op.nq = k;
+  std::vector<Mat> kraus = kraus_in;
+  if (k == 1) {
+    op.q[0] = qubits[0];
+    op.R = ptm(1, kraus, adj);
+    if (unitary) {
+      // a unitary conjugation fixes the identity and is trace preserving
+      op.R[0] = 1.0;
+      op.R[1] = op.R[2] = op.R[3] = op.R[4] = op.R[8] = op.R[12] = 0.0;
+      op.kind = OP_PTM1_U;
+    } else {
+      op.kind = is_ad_pattern(op.R) ? OP_PTM1_AD : OP_PTM1;
+    }
+  } else {
+    if (qubits[0] < qubits[1]) {
+      op.q[0] = qubits[0];
+      op.q[1] = qubits[1];
+    } else {
+      op.q[0] = qubits[1];
+      op.q[1] = qubits[0];
+      for (auto& K : kraus) K = swap_local_bits(K);
+    }
+    if (kraus.size() == 1) {
+      // direct form h -> V h V^dagger (Eq. 2 with r = 1)
+      const Mat V = adj ? dagger(kraus[0], 4) : kraus[0];
+      op.kind = OP_U2;
+      op.coef.resize(32);
+      for (int i = 0; i < 16; ++i) {
+        op.coef[2 * i] = V[i].real();
+        op.coef[2 * i + 1] = V[i].imag();
+      }
+    } else {
+      const std::vector<double> R = ptm(2, kraus, adj);
+      op.kind = OP_PTM2;
+      op.coef.resize(256);
+      for (int i = 0; i < 256; ++i) op.coef[i] = 0.25 * R[i];
+    }
+  }
+  *out = std::move(op);
+  return ORKAN_OK;
+}
+
+// An AD-form op with closed-form coefficients (projectors, renormalisation).
+HostOp make_ad_op(int q, const double R[16]) {
+  HostOp op;
+  op.nq = 1;
+  op.q[0] = q;
+  op.kind = OP_PTM1_AD;
+  op.R.assign(R, R + 16);
+  return op;
+}
+
+int reduce_diag(orkan_ctx* h, int q, double out[4]) {
+  int st = flush_pending(h);
+  if (st != ORKAN_OK) return st;
+  ORKAN_CUDA(launch_reduce_diag(h->dtype, h->d_state, h->g, q, h->d_partials, h->d_res, h->stream));
+  h->n_launches += 2;
+  ORKAN_CUDA(cudaMemcpyAsync(h->h_res, h->d_res, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < 4; ++i) out[i] = h->h_res[i];
+  return ORKAN_OK;
+}
+
+int setup_handle(orkan_ctx* c) {
+  ORKAN_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  c->own_stream = true;
+  if (cudaMalloc(&c->d_partials, sizeof(double) * 4 * kRedBlocks) != cudaSuccess)
+    return fail(ORKAN_ENOMEM, "cudaMalloc(partials) failed");
+  if (cudaMalloc(&c->d_res, sizeof(double) * 4) != cudaSuccess) return fail(ORKAN_ENOMEM, "cudaMalloc(res) failed");
+  if (cudaMallocHost(&c->h_res, sizeof(double) * 4) != cudaSuccess)
+    return fail(ORKAN_ENOMEM, "cudaMallocHost(res) failed");
+  return ORKAN_OK;
+}
+
+void release_handle(orkan_ctx* c) {
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& p : c->ev_used) {
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  for (auto e : c->ev_free) cudaEventDestroy(e);
+  if (c->d_state && !c->external) cudaFree(c->d_state);
+  if (c->d_partials) cudaFree(c->d_partials);
+  if (c->d_res) cudaFree(c->d_res);
+  if (c->h_res) cudaFreeHost(c->h_res);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+bool geometry(int n, int tile_log2, Geometry* g) {
+  if (tile_log2 == 0) tile_log2 = 5;
+  if (n < 1 || n > 24 || tile_log2 < 2 || tile_log2 > 5) return false;
+  g->n = n;
+  g->m = tile_log2;
+  g->N = int64_t(1) << n;
+  g->Nt = n > tile_log2 ? (int64_t(1) << (n - tile_log2)) : 1;
+  g->ntiles = g->Nt * (g->Nt + 1) / 2;
+  return true;
+}
+
+int common_alloc(int n, int dtype, int tile_log2, void* dev_ptr, size_t bytes, orkan_h* out) {
+  if (!out) return fail(ORKAN_EINVAL, "null output handle");
+  *out = nullptr;
+  Geometry g;
+  if (!valid_dtype(dtype) || !geometry(n, tile_log2, &g)) return fail(ORKAN_EINVAL, "bad n / dtype / tile_log2");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(ORKAN_ENODEV, "no CUDA device");
+  orkan_ctx* c = new (std::nothrow) orkan_ctx;
+  if (!c) return fail(ORKAN_ENOMEM, "host allocation failed");
+  c->g = g;
+  c->dtype = dtype;
+  c->bytes = size_t(g.ntiles) << (2 * g.m);
+  c->bytes *= elem_size(dtype);
+  cudaGetDevice(&c->device);
+  int st = setup_handle(c);
+  if (st != ORKAN_OK) {
+    release_handle(c);
+    return st;
+  }
+  if (dev_ptr) {
+    if (bytes < c->bytes || (reinterpret_cast<uintptr_t>(dev_ptr) & 255) != 0) {
+      release_handle(c);
+      return fail(ORKAN_EINVAL, "external buffer too small or not 256-byte aligned");
+    }
+    c->d_state = dev_ptr;
+    c->external = true;
+  } else if (cudaMalloc(&c->d_state, c->bytes) != cudaSuccess) {
+    cudaGetLastError();
+    release_handle(c);
+    return fail(ORKAN_ENOMEM, "cudaMalloc of the tiled state failed");
+  }
+  *out = c;
+  return ORKAN_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* orkan_strerror(int status) {
+  switch (status) {
+    case ORKAN_OK: return "ok";
+    case ORKAN_EINVAL: return "invalid argument";
+    case ORKAN_ENOMEM: return "out of memory";
+    case ORKAN_ECUDA: return "CUDA error";
+    case ORKAN_EZEROPROB: return "zero-probability outcome";
+    case ORKAN_EPICTURE: return "operation not defined in this picture";
+    case ORKAN_ENODEV: return "no CUDA device";
+  }
+  return "unknown status";
+}
+
+const char* orkan_last_error(void) { return g_last_error.c_str(); }
+
+size_t orkan_bytes(int n, int dtype, int tile_log2) {
+  Geometry g;
+  if (!valid_dtype(dtype) || !geometry(n, tile_log2, &g)) return 0;
+  return (size_t(g.ntiles) << (2 * g.m)) * size_t(elem_size(dtype));
+}
+
+int64_t orkan_num_tiles(int n, int tile_log2) {
+  Geometry g;
+  if (!geometry(n, tile_log2, &g)) return -1;
+  return g.ntiles;
+}
+
+int64_t orkan_element_offset(int n, int tile_log2, int64_t i, int64_t j, int* conj) {
+  Geometry g;
+  if (!geometry(n, tile_log2, &g) || i < 0 || j < 0 || i >= g.N || j >= g.N) return -1;
+  int cj = 0;
+  if (i < j) {
+    std::swap(i, j);
+    cj = 1;
+  }
+  if (conj) *conj = cj;
+  const int64_t ti = i >> g.m, tj = j >> g.m, M = int64_t(1) << g.m;
+  return ((ti * (ti + 1) / 2 + tj) << (2 * g.m)) + (i & (M - 1)) * M + (j & (M - 1));
+}
+
+uint64_t orkan_insert_bits(uint64_t s, uint64_t a, int k, const int* pos) {
+  // Subroutine 1: for each active position (ascending), split the index there
+  // and drop bit l of a into the gap.
+  uint64_t global = s;
+  for (int l = 0; l < k; ++l) {
+    const int p = pos[l];
+    const uint64_t right = ((uint64_t(1) << p) - 1) & global;
+    uint64_t left = (global >> p) << 1;
+    left |= (a >> l) & 1;
+    left <<= p;
+    global = left | right;
+  }
+  return global;
+}
+
+int orkan_ptm(int k, int r, const double* K, int adjoint, double* out) {
+  if (k < 1 || k > 2 || r < 1 || r > (1 << (2 * k)) || !K || !out) return fail(ORKAN_EINVAL, "bad ptm arguments");
+  const int d = 1 << k;
+  std::vector<Mat> kraus;
+  for (int a = 0; a < r; ++a) kraus.push_back(read_mat(K + 2 * d * d * a, d));
+  const std::vector<double> R = ptm(k, kraus, adjoint != 0);
+  std::copy(R.begin(), R.end(), out);
+  return ORKAN_OK;
+}
+
+int orkan_alloc(int n, int dtype, int tile_log2, orkan_h* out) {
+  return common_alloc(n, dtype, tile_log2, nullptr, 0, out);
+}
+
+int orkan_alloc_external(int n, int dtype, int tile_log2, void* dev_ptr, size_t bytes, orkan_h* out) {
+  if (!dev_ptr) return fail(ORKAN_EINVAL, "null device pointer");
+  return common_alloc(n, dtype, tile_log2, dev_ptr, bytes, out);
+}
+
+int orkan_free(orkan_h h) {
+  if (!h) return ORKAN_OK;
+  h->pending.clear();
+  release_handle(h);
+  return ORKAN_OK;
+}
+
+int orkan_set_stream(orkan_h h, void* cuda_stream) {
+  if (int st = check_handle(h)) return st;
+  if (int st = flush_pending(h)) return st;
+  if (h->own_stream && h->stream) {
+    ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+    cudaStreamDestroy(h->stream);
+  }
+  h->own_stream = false;
+  h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  return ORKAN_OK;
+}
+
+int orkan_set_fusion(orkan_h h, int max_ops, int compose) {
+  if (int st = check_handle(h)) return st;
+  if (max_ops < 1 || max_ops > kMaxOps) return fail(ORKAN_EINVAL, "max_ops must be in 1..16");
+  if (int st = flush_pending(h)) return st;
+  h->fusion = max_ops;
+  h->compose = compose != 0;
+  return ORKAN_OK;
+}
+
+int orkan_get_info(orkan_h h, int* n, int* dtype, int* tile_log2, int* picture) {
+  if (int st = check_handle(h)) return st;
+  if (n) *n = h->g.n;
+  if (dtype) *dtype = h->dtype;
+  if (tile_log2) *tile_log2 = h->g.m;
+  if (picture) *picture = h->picture;
+  return ORKAN_OK;
+}
+
+void* orkan_device_ptr(orkan_h h) { return h ? h->d_state : nullptr; }
+
+int orkan_init_state(orkan_h h, int kind, const double* data) {
+  if (int st = check_handle(h)) return st;
+  h->pending.clear();
+  h->picture = ORKAN_STATE;
+  switch (kind) {
+    case ORKAN_INIT_ZERO:
+      ORKAN_CUDA(launch_zero(h->dtype, h->d_state, h->g, h->stream));
+      ORKAN_CUDA(launch_set_diag(h->dtype, h->d_state, h->g, 0, 1.0, h->stream));
+      h->n_launches += 2;
+      return ORKAN_OK;
+    case ORKAN_INIT_MAXMIXED:
+      ORKAN_CUDA(launch_zero(h->dtype, h->d_state, h->g, h->stream));
+      ORKAN_CUDA(launch_fill_diag(h->dtype, h->d_state, h->g, 1.0 / double(h->g.N), h->stream));
+      h->n_launches += 2;
+      return ORKAN_OK;
+    case ORKAN_INIT_DENSE:
+    case ORKAN_INIT_PURE: {
+      if (!data) return fail(ORKAN_EINVAL, "data required");
+      const size_t count = kind == ORKAN_INIT_DENSE ? size_t(h->g.N) * size_t(h->g.N) : size_t(h->g.N);
+      double* tmp = nullptr;
+      if (cudaMalloc(&tmp, count * 16) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ORKAN_ENOMEM, "cudaMalloc(upload) failed");
+      }
+      cudaError_t e = cudaMemcpyAsync(tmp, data, count * 16, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess)
+        e = kind == ORKAN_INIT_DENSE ? launch_from_dense(h->dtype, h->d_state, h->g, tmp, h->stream)
+                                     : launch_from_pure(h->dtype, h->d_state, h->g, tmp, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      cudaFree(tmp);
+      if (e != cudaSuccess) return cuda_fail(e, "init_state");
+      h->n_launches += 1;
+      return ORKAN_OK;
+    }
+  }
+  return fail(ORKAN_EINVAL, "unknown init kind");
+}
+
+int orkan_init_observable(orkan_h h, int nterms, const char* paulis, const double* coeffs) {
+  if (int st = check_handle(h)) return st;
+  if (nterms < 0 || (nterms > 0 && (!paulis || !coeffs))) return fail(ORKAN_EINVAL, "bad Pauli sum");
+  const int n = h->g.n;
+  struct Term {
+    uint64_t x, z, y, ny;
+    double c;
+  };
+  std::vector<Term> terms;
+  for (int t = 0; t < nterms; ++t) {
+    Term tm{0, 0, 0, 0, coeffs[t]};
+    for (int l = 0; l < n; ++l) {
+      const char ch = paulis[size_t(t) * n + l];
+      const uint64_t bit = uint64_t(1) << l;
+      if (ch == 'I') continue;
+      if (ch == 'X') tm.x |= bit;
+      else if (ch == 'Y') { tm.x |= bit; tm.y |= bit; tm.ny += 1; }
+      else if (ch == 'Z') tm.z |= bit;
+      else return fail(ORKAN_EINVAL, "Pauli characters must be I, X, Y or Z");
+    }
+    terms.push_back(tm);
+  }
+  std::stable_sort(terms.begin(), terms.end(), [](const Term& a, const Term& b) { return a.x < b.x; });
+  h->pending.clear();
+  h->picture = ORKAN_OBSERVABLE;
+  ORKAN_CUDA(launch_zero(h->dtype, h->d_state, h->g, h->stream));
+  h->n_launches += 1;
+  if (terms.empty()) return ORKAN_OK;
+  std::vector<uint64_t> masks;
+  std::vector<double> cs;
+  for (const auto& t : terms) {
+    masks.insert(masks.end(), {t.x, t.z, t.y, t.ny});
+    cs.push_back(t.c);
+  }
+  uint64_t* dm = nullptr;
+  double* dc = nullptr;
+  if (cudaMalloc(&dm, masks.size() * 8) != cudaSuccess || cudaMalloc(&dc, cs.size() * 8) != cudaSuccess) {
+    cudaGetLastError();
+    if (dm) cudaFree(dm);
+    return fail(ORKAN_ENOMEM, "cudaMalloc(pauli terms) failed");
+  }
+  cudaError_t e = cudaMemcpyAsync(dm, masks.data(), masks.size() * 8, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dc, cs.data(), cs.size() * 8, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = launch_pauli_sum(h->dtype, h->d_state, h->g, int(terms.size()), dm, dc, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(dm);
+  cudaFree(dc);
+  if (e != cudaSuccess) return cuda_fail(e, "init_observable");
+  h->n_launches += 1;
+  return ORKAN_OK;
+}
+
+int orkan_load_tiled(orkan_h h, const void* host_src, int picture) {
+  if (int st = check_handle(h)) return st;
+  if (!host_src || (picture != ORKAN_STATE && picture != ORKAN_OBSERVABLE)) return fail(ORKAN_EINVAL, "bad args");
+  h->pending.clear();
+  h->picture = picture;
+  ORKAN_CUDA(cudaMemcpyAsync(h->d_state, host_src, h->bytes, cudaMemcpyHostToDevice, h->stream));
+  ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+  return ORKAN_OK;
+}
+
+int orkan_store_tiled(orkan_h h, void* host_dst) {
+  if (int st = check_handle(h)) return st;
+  if (!host_dst) return fail(ORKAN_EINVAL, "null destination");
+  if (int st = flush_pending(h)) return st;
+  ORKAN_CUDA(cudaMemcpyAsync(host_dst, h->d_state, h->bytes, cudaMemcpyDeviceToHost, h->stream));
+  ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+  return ORKAN_OK;
+}
+
+int orkan_apply_unitary(orkan_h h, int k, const int* qubits, const double* U) {
+  if (int st = check_handle(h)) return st;
+  if (int st = check_qubits(h, k, qubits)) return st;
+  if (!U) return fail(ORKAN_EINVAL, "null matrix");
+  HostOp op;
+  if (int st = make_op(h, k, qubits, {read_mat(U, 1 << k)}, true, &op)) return st;
+  return enqueue(h, std::move(op));
+}
+
+int orkan_apply_kraus(orkan_h h, int k, const int* qubits, int r, const double* K) {
+  if (int st = check_handle(h)) return st;
+  if (int st = check_qubits(h, k, qubits)) return st;
+  if (!K || r < 1 || r > (1 << (2 * k))) return fail(ORKAN_EINVAL, "need 1 <= r <= 4^k Kraus operators");
+  const int d = 1 << k;
+  std::vector<Mat> kraus;
+  for (int a = 0; a < r; ++a) kraus.push_back(read_mat(K + 2 * d * d * a, d));
+  HostOp op;
+  if (int st = make_op(h, k, qubits, kraus, false, &op)) return st;
+  return enqueue(h, std::move(op));
+}
+
+static int named_channel(orkan_h h, int q, const std::vector<Mat>& kraus) {
+  if (int st = check_handle(h)) return st;
+  if (int st = check_qubits(h, 1, &q)) return st;
+  HostOp op;
+  if (int st = make_op(h, 1, &q, kraus, false, &op)) return st;
+  op.kind = OP_PTM1_AD;   // diagonal / amplitude-mixing structure holds exactly for these sets
+  return enqueue(h, std::move(op));
+}
+
+int orkan_depolarize(orkan_h h, int q, double p) {
+  if (!(p >= 0.0 && p <= 1.0)) return fail(ORKAN_EINVAL, "p must be in [0, 1]");
+  if (int st = check_handle(h)) return st;
+  if (int st = check_qubits(h, 1, &q)) return st;
+  // Kraus sqrt(1-p) I, sqrt(p/3) {X, Y, Z} (Sec. IV-A) have the self-adjoint
+  // transfer matrix diag(1, f, f, f), f = 1 - 4p/3, used in closed form.
+  const double f = 1.0 - 4.0 * p / 3.0;
+  const double R[16] = {1, 0, 0, 0, 0, f, 0, 0, 0, 0, f, 0, 0, 0, 0, f};
+  return enqueue(h, make_ad_op(q, R));
+}
+
+int orkan_dephase(orkan_h h, int q, double p) {
+  if (!(p >= 0.0 && p <= 1.0)) return fail(ORKAN_EINVAL, "p must be in [0, 1]");
+  const double a = std::sqrt(1.0 - p), b = std::sqrt(p);
+  return named_channel(h, q, {{a, 0, 0, a}, {b, 0, 0, -b}});
+}
+
+int orkan_amplitude_damp(orkan_h h, int q, double gamma) {
+  if (!(gamma >= 0.0 && gamma <= 1.0)) return fail(ORKAN_EINVAL, "gamma must be in [0, 1]");
+  const double s = std::sqrt(1.0 - gamma), g = std::sqrt(gamma);
+  return named_channel(h, q, {{1, 0, 0, s}, {0, g, 0, 0}});
+}
+
+int orkan_measure(orkan_h h, int q, double u, int* outcome, double* prob) {
+  if (int st = check_handle(h)) return st;
+  if (h->picture != ORKAN_STATE) return fail(ORKAN_EPICTURE, "measure needs a state handle (use orkan_project)");
+  if (int st = check_qubits(h, 1, &q)) return st;
+  if (!(u >= 0.0 && u < 1.0)) return fail(ORKAN_EINVAL, "u must be in [0, 1)");
+  double r[4];
+  if (int st = reduce_diag(h, q, r)) return st;
+  const double p0 = r[2], p1 = r[3], tot = p0 + p1;
+  if (!(tot > 0.0)) return fail(ORKAN_EZEROPROB, "both outcomes have zero probability");
+  const int b = (u * tot < p0) ? 0 : 1;
+  const double pb = b ? p1 : p0;
+  if (!(pb > 1e-300)) return fail(ORKAN_EZEROPROB, "selected outcome has zero probability");
+  const double s = 1.0 / pb;
+  // transfer matrix of Pi_b . Pi_b / p_b
+  const double sg = b ? -0.5 * s : 0.5 * s;
+  const double R[16] = {0.5 * s, 0, 0, sg, 0, 0, 0, 0, 0, 0, 0, 0, sg, 0, 0, 0.5 * s};
+  if (int st = enqueue(h, make_ad_op(q, R))) return st;
+  if (outcome) *outcome = b;
+  if (prob) *prob = pb / tot;
+  return ORKAN_OK;
+}
+
+int orkan_project(orkan_h h, int q, int outcome) {
+  if (int st = check_handle(h)) return st;
+  if (int st = check_qubits(h, 1, &q)) return st;
+  if (outcome != 0 && outcome != 1) return fail(ORKAN_EINVAL, "outcome must be 0 or 1");
+  const double sg = outcome ? -0.5 : 0.5;
+  const double R[16] = {0.5, 0, 0, sg, 0, 0, 0, 0, 0, 0, 0, 0, sg, 0, 0, 0.5};
+  return enqueue(h, make_ad_op(q, R));
+}
+
+int orkan_trace(orkan_h h, double* re, double* im) {
+  if (int st = check_handle(h)) return st;
+  double r[4];
+  if (int st = reduce_diag(h, -1, r)) return st;
+  if (re) *re = r[0];
+  if (im) *im = r[1];
+  return ORKAN_OK;
+}
+
+int orkan_expect_pauli(orkan_h h, const char* pauli, double* out) {
+  if (int st = check_handle(h)) return st;
+  if (!pauli || !out) return fail(ORKAN_EINVAL, "null argument");
+  uint64_t x = 0, z = 0, y = 0;
+  int ny = 0;
+  for (int l = 0; l < h->g.n; ++l) {
+    const char ch = pauli[l];
+    const uint64_t bit = uint64_t(1) << l;
+    if (ch == 'I') continue;
+    if (ch == 'X') x |= bit;
+    else if (ch == 'Y') { x |= bit; y |= bit; ++ny; }
+    else if (ch == 'Z') z |= bit;
+    else return fail(ORKAN_EINVAL, "Pauli characters must be I, X, Y or Z");
+  }
+  if (pauli[h->g.n] != '\0') return fail(ORKAN_EINVAL, "Pauli string must have n characters");
+  if (int st = flush_pending(h)) return st;
+  ORKAN_CUDA(launch_reduce_pauli(h->dtype, h->d_state, h->g, x, z, y, h->d_partials, h->d_res, h->stream));
+  h->n_launches += 2;
+  ORKAN_CUDA(cudaMemcpyAsync(h->h_res, h->d_res, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+  const double sr = h->h_res[0], si = h->h_res[1];
+  // tr(P H) = i^{nY} S
+  switch (ny & 3) {
+    case 0: *out = sr; break;
+    case 1: *out = -si; break;
+    case 2: *out = -sr; break;
+    default: *out = si; break;
+  }
+  return ORKAN_OK;
+}
+
+int orkan_expect(orkan_h rho, orkan_h O, double* out) {
+  if (int st = check_handle(rho)) return st;
+  if (int st = check_handle(O)) return st;
+  if (!out) return fail(ORKAN_EINVAL, "null output");
+  if (rho->g.n != O->g.n || rho->g.m != O->g.m || rho->dtype != O->dtype)
+    return fail(ORKAN_EINVAL, "operands differ in n, tile size or dtype");
+  if (int st = flush_pending(O)) return st;
+  if (O != rho) ORKAN_CUDA(cudaStreamSynchronize(O->stream));
+  if (int st = flush_pending(rho)) return st;
+  ORKAN_CUDA(launch_reduce_expect(rho->dtype, rho->d_state, O->d_state, rho->g, rho->d_partials, rho->d_res,
+                                  rho->stream));
+  rho->n_launches += 2;
+  ORKAN_CUDA(cudaMemcpyAsync(rho->h_res, rho->d_res, sizeof(double), cudaMemcpyDeviceToHost, rho->stream));
+  ORKAN_CUDA(cudaStreamSynchronize(rho->stream));
+  *out = rho->h_res[0];
+  return ORKAN_OK;
+}
+
+int orkan_to_dense(orkan_h h, double* out) {
+  if (int st = check_handle(h)) return st;
+  if (!out) return fail(ORKAN_EINVAL, "null output");
+  if (int st = flush_pending(h)) return st;
+  const size_t bytes = size_t(h->g.N) * size_t(h->g.N) * 16;
+  double* tmp = nullptr;
+  if (cudaMalloc(&tmp, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ORKAN_ENOMEM, "cudaMalloc(dense) failed");
+  }
+  cudaError_t e = launch_to_dense(h->dtype, h->d_state, h->g, tmp, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "to_dense");
+  h->n_launches += 1;
+  return ORKAN_OK;
+}
+
+int orkan_get_elements(orkan_h h, int64_t count, const int64_t* rows, const int64_t* cols, double* out) {
+  if (int st = check_handle(h)) return st;
+  if (count < 0 || (count > 0 && (!rows || !cols || !out))) return fail(ORKAN_EINVAL, "bad element list");
+  if (count == 0) return flush_pending(h);
+  for (int64_t t = 0; t < count; ++t)
+    if (rows[t] < 0 || rows[t] >= h->g.N || cols[t] < 0 || cols[t] >= h->g.N)
+      return fail(ORKAN_EINVAL, "element index out of range");
+  if (int st = flush_pending(h)) return st;
+  int64_t* d_idx = nullptr;
+  double* d_out = nullptr;
+  if (cudaMalloc(&d_idx, size_t(count) * 16) != cudaSuccess || cudaMalloc(&d_out, size_t(count) * 16) != cudaSuccess) {
+    cudaGetLastError();
+    if (d_idx) cudaFree(d_idx);
+    return fail(ORKAN_ENOMEM, "cudaMalloc(gather) failed");
+  }
+  cudaError_t e = cudaMemcpyAsync(d_idx, rows, size_t(count) * 8, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_idx + count, cols, size_t(count) * 8, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = launch_gather(h->dtype, h->d_state, h->g, count, d_idx, d_idx + count, d_out, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, size_t(count) * 16, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d_idx);
+  cudaFree(d_out);
+  if (e != cudaSuccess) return cuda_fail(e, "get_elements");
+  h->n_launches += 1;
+  return ORKAN_OK;
+}
+
+int orkan_flush(orkan_h h) {
+  if (int st = check_handle(h)) return st;
+  return flush_pending(h);
+}
+
+int orkan_sync(orkan_h h) {
+  if (int st = check_handle(h)) return st;
+  if (int st = flush_pending(h)) return st;
+  ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+  return ORKAN_OK;
+}
+
+int orkan_stats(orkan_h h, int64_t* passes, int64_t* ops, int64_t* launches) {
+  if (int st = check_handle(h)) return st;
+  if (passes) *passes = h->n_passes;
+  if (ops) *ops = h->n_ops;
+  if (launches) *launches = h->n_launches;
+  return ORKAN_OK;
+}
+
+int orkan_set_timing(orkan_h h, int enable) {
+  if (int st = check_handle(h)) return st;
+  if (int st = flush_pending(h)) return st;
+  h->timing = enable != 0;
+  return ORKAN_OK;
+}
+
+int orkan_pass_time(orkan_h h, double* ms, int64_t* count) {
+  if (int st = check_handle(h)) return st;
+  if (int st = flush_pending(h)) return st;
+  ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+  double total = 0.0;
+  for (auto& p : h->ev_used) {
+    float t = 0.0f;
+    ORKAN_CUDA(cudaEventElapsedTime(&t, p.first, p.second));
+    total += t;
+    h->ev_free.push_back(p.first);
+    h->ev_free.push_back(p.second);
+  }
+  if (count) *count = int64_t(h->ev_used.size());
+  h->ev_used.clear();
+  if (ms) *ms = total;
+  return ORKAN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Internal definitions shared by the host planner and the CUDA kernels of the
+// Orkan GB300 library.  Nothing here is part of the public C ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace orkan {
+
+// Storage / arithmetic policies (public values of orkan_dtype).
+enum Dtype : int { DT_C128 = 0, DT_C64 = 1, DT_DF64 = 2 };
+
+// Per-op arithmetic forms.  Every form is applied to a 2^k x 2^k block of the
+// operator (Eq. 2, Sec. II-A); the coefficients are prepared on the host in
+// FP64 from the Kraus operators.
+//   PTM1    : generic single-qubit map, Pauli transfer matrix R/2 (4x4 real)
+//   PTM1_U  : unitary single-qubit conjugation, R = 1 (+) R3, coefficients R3/2
+//   PTM1_AD : maps that only mix (h00, h11) and scale h01 / h10:
+//             h00' = al h00 + be h11, h11' = ga h00 + de h11,
+//             h01' = (rho - i sig) h01, h10' = (rho + i sig) h10
+//             (depolarising, dephasing, amplitude damping, projectors, Rz)
+//   U2      : two-qubit unitary, direct form V h V^dagger (Eq. 2 with r = 1)
+//   PTM2    : generic two-qubit map, Pauli transfer matrix R/4 (16x16 real)
+enum OpKind : int { OP_PTM1 = 0, OP_PTM1_U = 1, OP_PTM1_AD = 2, OP_U2 = 3, OP_PTM2 = 4 };
+
+constexpr int kMaxOps = 16;     // ops fused into one pass
+constexpr int kMaxCoef = 640;   // 8-byte coefficient slots per pass
+constexpr int kThreads = 256;   // threads per CTA of the pass kernel
+
+inline int coef_slots(int kind) {
+  switch (kind) {
+    case OP_PTM1: return 16;
+    case OP_PTM1_U: return 9;
+    case OP_PTM1_AD: return 6;
+    case OP_U2: return 32;      // 16 complex entries, re/im interleaved
+    case OP_PTM2: return 256;
+  }
+  return 0;
+}
+
+struct PassOp {
+  int32_t kind;
+  int32_t nq;        // 1 or 2
+  int32_t rbit[2];   // bit positions in the group row index (ascending)
+  int32_t cbit[2];   // bit positions in the group column index (ascending)
+  int32_t coef;      // first coefficient slot
+  int32_t pad;
+};
+
+// One fused pass over the whole tiled operator.  A work item is one tile
+// group -- the 2^h x 2^h tiles obtained by inserting every combination of the
+// h high-qubit bits into a base tile pair (ti, tj) of the compressed grid, as
+// in Algorithm 3 -- restricted to a chunk of 2^rows_log2 rows of each tile.
+struct PassDesc {
+  int64_t n_items;     // groups * chunks
+  int64_t nt_c;        // edge of the compressed tile grid (Nt >> h)
+  int32_t m;           // tile_log2
+  int32_t h;           // number of high (cross-tile) qubits, 0..2
+  int32_t hpos[2];     // tile-index bit positions a - m of the high qubits (ascending)
+  int32_t rows_log2;   // rows of each tile held per work item
+  int32_t chunks_log2; // m - rows_log2
+  int32_t nops;
+  int32_t skip_diag;   // 1: chunked pass; diagonal groups run in pass_kernel_diag
+  PassOp ops[kMaxOps];
+  double coef[kMaxCoef];   // F64: double; DF64: float2 (hi, lo); C64: float in the low half
+};
+
+// Launchers (pass_kernels.cu).  Return cudaSuccess or the launch error;
+// *launches receives the number of kernels launched (1 or 2).
+cudaError_t launch_pass(int dtype, void* state, const PassDesc& d, cudaStream_t s, int* launches);
+
+// Auxiliary kernels (aux_kernels.cu).
+struct Geometry {
+  int n;
+  int m;
+  int64_t N;       // 2^n
+  int64_t Nt;      // tile rows (>= 1)
+  int64_t ntiles;  // Nt (Nt + 1) / 2
+};
+cudaError_t launch_zero(int dtype, void* state, const Geometry& g, cudaStream_t s);
+cudaError_t launch_set_diag(int dtype, void* state, const Geometry& g, int64_t i, double re, cudaStream_t s);
+cudaError_t launch_fill_diag(int dtype, void* state, const Geometry& g, double re, cudaStream_t s);
+cudaError_t launch_from_dense(int dtype, void* state, const Geometry& g, const double* dense_dev, cudaStream_t s);
+cudaError_t launch_from_pure(int dtype, void* state, const Geometry& g, const double* psi_dev, cudaStream_t s);
+cudaError_t launch_to_dense(int dtype, const void* state, const Geometry& g, double* dense_dev, cudaStream_t s);
+cudaError_t launch_gather(int dtype, const void* state, const Geometry& g, int64_t count, const int64_t* rows_dev,
+                          const int64_t* cols_dev, double* out_dev, cudaStream_t s);
+cudaError_t launch_pauli_sum(int dtype, void* state, const Geometry& g, int nterms, const uint64_t* masks_dev,
+                             const double* coeffs_dev, cudaStream_t s);
+// Reductions write into a device double[4] result (after a fixed-order two-stage reduction).
+//   diag:  res = {sum Re h_ii, sum Im h_ii, sum_{bit q of i = 0} Re h_ii, sum_{bit q = 1} Re h_ii}
+//   pauli: res = {Re S, Im S} with S = sum_i sign(i) h[i ^ x, i]
+//   expect: res = {sum_tiles w Re <O_t, rho_t>_F}
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs; fixed so the summation order is fixed
+cudaError_t launch_reduce_diag(int dtype, const void* state, const Geometry& g, int q, double* partials,
+                               double* res, cudaStream_t s);
+cudaError_t launch_reduce_pauli(int dtype, const void* state, const Geometry& g, uint64_t xmask, uint64_t zmask,
+                                uint64_t ymask, double* partials, double* res, cudaStream_t s);
+cudaError_t launch_reduce_expect(int dtype, const void* rho, const void* O, const Geometry& g, double* partials,
+                                 double* res, cudaStream_t s);
+
+}  // namespace orkan

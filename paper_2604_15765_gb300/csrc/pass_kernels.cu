@@ -1,0 +1,608 @@
+// Fused k-local conjugation passes over the tiled lower-triangle layout.
+//
+// Sec. III-B stores tiles T[ti, tj], ti >= tj, row-major, elements row-major.
+// Sec. III-C splits an update into intra-tile work (all targets below m,
+// Algorithm 2) and cross-tile work (a target a >= m couples the tiles whose
+// indices differ in bit a - m, Algorithm 3, with subcases A / B / C depending
+// on whether the partner tile T[ti0, tj1] is stored, is the adjoint of a
+// stored tile, or is the adjoint of T[ti1, tj0] itself).
+//
+// GPU design: one CTA owns one *tile group* at a time: the 2^h x 2^h tiles
+// (h = number of high qubits in the pass, 0..2) whose grid indices share the
+// bits outside the high positions.  The group is staged in shared memory in
+// its *logical* orientation: a tile of the group that lies in the upper
+// triangle is loaded from its stored partner transposed and conjugated
+// (this covers subcases B and C uniformly), so that every op of the fused
+// pass sees a plain (2^h M) x (2^h M) hermitian block and applies Eq. (2) to
+// its 2^k x 2^k sub-blocks.  Only stored tiles are written back, each exactly
+// once: in a diagonal group (ti == tj before bit insertion) the upper slots
+// are mirrors of lower slots of the same group and are not written.
+//
+// Shared memory holds each slot row-major with the 16-byte (8-byte) element
+// index XOR-swizzled by the row, so that transposed loads/stores and
+// strided butterfly accesses hit distinct banks.
+#include "orkan_internal.h"
+#include "numeric.cuh"
+#include "device_util.cuh"
+
+namespace orkan {
+namespace {
+
+// Subroutine 1 with a zero bit: make room at position p.
+__device__ __forceinline__ int64_t ins0(int64_t x, int p) {
+  const int64_t low = x & ((int64_t(1) << p) - 1);
+  return ((x >> p) << (p + 1)) | low;
+}
+__device__ __forceinline__ int ins0i(int x, int p) {
+  const int low = x & ((1 << p) - 1);
+  return ((x >> p) << (p + 1)) | low;
+}
+
+struct SMap {
+  int rl, m, H, sw;
+  __device__ __forceinline__ int idx(int li, int lj) const {
+    const int x = li >> rl, r = li & ((1 << rl) - 1);
+    const int y = lj >> m, c = lj & ((1 << m) - 1);
+    const int slot = (x << H) | y;
+    return (((slot << rl) | r) << m) | (c ^ (r & sw));
+  }
+};
+
+// ------------------------------------------------------------------ op bodies
+// A 2x2 block [[a, b], [c, d]] in Pauli coordinates s_k = 2 z_k:
+//   s0 = a + d, s1 = b + c, s2 = i (b - c), s3 = a - d,
+// and back: a = z0 + z3, d = z0 - z3, b = z1 - i z2, c = z1 + i z2.
+
+template <class P>
+__device__ __forceinline__ void body_ptm1(Cx<P>& a, Cx<P>& b, Cx<P>& c, Cx<P>& d, const double* cf) {
+  using R = typename P::Real;
+  R sr[4], si[4];
+  sr[0] = P::add(a.re, d.re); si[0] = P::add(a.im, d.im);
+  sr[1] = P::add(b.re, c.re); si[1] = P::add(b.im, c.im);
+  sr[2] = P::sub(c.im, b.im); si[2] = P::sub(b.re, c.re);
+  sr[3] = P::sub(a.re, d.re); si[3] = P::sub(a.im, d.im);
+  R zr[4], zi[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    R ar = P::mul(sr[0], P::coef(cf, 4 * i));
+    R ai = P::mul(si[0], P::coef(cf, 4 * i));
+#pragma unroll
+    for (int j = 1; j < 4; ++j) {
+      ar = P::mac(ar, sr[j], P::coef(cf, 4 * i + j));
+      ai = P::mac(ai, si[j], P::coef(cf, 4 * i + j));
+    }
+    zr[i] = P::norm(ar);
+    zi[i] = P::norm(ai);
+  }
+  a.re = P::add(zr[0], zr[3]); a.im = P::add(zi[0], zi[3]);
+  d.re = P::sub(zr[0], zr[3]); d.im = P::sub(zi[0], zi[3]);
+  b.re = P::add(zr[1], zi[2]); b.im = P::sub(zi[1], zr[2]);
+  c.re = P::sub(zr[1], zi[2]); c.im = P::add(zi[1], zr[2]);
+}
+
+template <class P>
+__device__ __forceinline__ void body_ptm1_u(Cx<P>& a, Cx<P>& b, Cx<P>& c, Cx<P>& d, const double* cf) {
+  using R = typename P::Real;
+  R sr[3], si[3];
+  sr[0] = P::add(b.re, c.re); si[0] = P::add(b.im, c.im);
+  sr[1] = P::sub(c.im, b.im); si[1] = P::sub(b.re, c.re);
+  sr[2] = P::sub(a.re, d.re); si[2] = P::sub(a.im, d.im);
+  const R z0r = P::half(P::add(a.re, d.re)), z0i = P::half(P::add(a.im, d.im));
+  R zr[3], zi[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R ar = P::mul(sr[0], P::coef(cf, 3 * i));
+    R ai = P::mul(si[0], P::coef(cf, 3 * i));
+#pragma unroll
+    for (int j = 1; j < 3; ++j) {
+      ar = P::mac(ar, sr[j], P::coef(cf, 3 * i + j));
+      ai = P::mac(ai, si[j], P::coef(cf, 3 * i + j));
+    }
+    zr[i] = P::norm(ar);
+    zi[i] = P::norm(ai);
+  }
+  a.re = P::add(z0r, zr[2]); a.im = P::add(z0i, zi[2]);
+  d.re = P::sub(z0r, zr[2]); d.im = P::sub(z0i, zi[2]);
+  b.re = P::add(zr[0], zi[1]); b.im = P::sub(zi[0], zr[1]);
+  c.re = P::sub(zr[0], zi[1]); c.im = P::add(zi[0], zr[1]);
+}
+
+template <class P>
+__device__ __forceinline__ void body_ptm1_ad(Cx<P>& a, Cx<P>& b, Cx<P>& c, Cx<P>& d, const double* cf) {
+  using R = typename P::Real;
+  const auto al = P::coef(cf, 0), be = P::coef(cf, 1), ga = P::coef(cf, 2), de = P::coef(cf, 3);
+  const auto rh = P::coef(cf, 4), sg = P::coef(cf, 5);
+  const R ar = P::norm(P::mac(P::mul(a.re, al), d.re, be));
+  const R ai = P::norm(P::mac(P::mul(a.im, al), d.im, be));
+  const R dr = P::norm(P::mac(P::mul(a.re, ga), d.re, de));
+  const R di = P::norm(P::mac(P::mul(a.im, ga), d.im, de));
+  // h01' = (rho - i sig) h01, h10' = (rho + i sig) h10
+  const R br = P::norm(P::mac(P::mul(b.re, rh), b.im, sg));
+  const R bi = P::norm(P::mac(P::mul(b.im, rh), P::neg(b.re), sg));
+  const R cr = P::norm(P::mac(P::mul(c.re, rh), P::neg(c.im), sg));
+  const R ci = P::norm(P::mac(P::mul(c.im, rh), c.re, sg));
+  a.re = ar; a.im = ai; d.re = dr; d.im = di;
+  b.re = br; b.im = bi; c.re = cr; c.im = ci;
+}
+
+// Two-qubit unitary, h <- V h V^dagger, in registers: first every row of h is
+// replaced by h[k,:] V^dagger, then every column by V (.)[:, j].
+template <class P>
+__device__ __forceinline__ void body_u2(Cx<P> (&h)[16], const double* cf) {
+  using R = typename P::Real;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    R tr[4], ti[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      // sum_l h[k][l] conj(V[j][l])
+      R accr = P::mul(h[4 * k].re, P::coef(cf, 2 * (4 * j)));
+      accr = P::mac(accr, h[4 * k].im, P::coef(cf, 2 * (4 * j) + 1));
+      R acci = P::mul(h[4 * k].im, P::coef(cf, 2 * (4 * j)));
+      acci = P::mac(acci, P::neg(h[4 * k].re), P::coef(cf, 2 * (4 * j) + 1));
+#pragma unroll
+      for (int l = 1; l < 4; ++l) {
+        const auto vr = P::coef(cf, 2 * (4 * j + l)), vi = P::coef(cf, 2 * (4 * j + l) + 1);
+        accr = P::mac(accr, h[4 * k + l].re, vr);
+        accr = P::mac(accr, h[4 * k + l].im, vi);
+        acci = P::mac(acci, h[4 * k + l].im, vr);
+        acci = P::mac(acci, P::neg(h[4 * k + l].re), vi);
+      }
+      tr[j] = P::norm(accr);
+      ti[j] = P::norm(acci);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { h[4 * k + j].re = tr[j]; h[4 * k + j].im = ti[j]; }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    R tr[4], ti[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      // sum_k V[i][k] Y[k][j]
+      const auto v0r = P::coef(cf, 2 * (4 * i)), v0i = P::coef(cf, 2 * (4 * i) + 1);
+      R accr = P::mul(h[j].re, v0r);
+      accr = P::mac(accr, P::neg(h[j].im), v0i);
+      R acci = P::mul(h[j].im, v0r);
+      acci = P::mac(acci, h[j].re, v0i);
+#pragma unroll
+      for (int k = 1; k < 4; ++k) {
+        const auto vr = P::coef(cf, 2 * (4 * i + k)), vi = P::coef(cf, 2 * (4 * i + k) + 1);
+        accr = P::mac(accr, h[4 * k + j].re, vr);
+        accr = P::mac(accr, P::neg(h[4 * k + j].im), vi);
+        acci = P::mac(acci, h[4 * k + j].im, vr);
+        acci = P::mac(acci, h[4 * k + j].re, vi);
+      }
+      tr[i] = P::norm(accr);
+      ti[i] = P::norm(acci);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { h[4 * i + j].re = tr[i]; h[4 * i + j].im = ti[i]; }
+  }
+}
+
+// Forward / inverse single-qubit Pauli transform on four complex values.
+template <class P>
+__device__ __forceinline__ void pauli_fwd(Cx<P>& a, Cx<P>& b, Cx<P>& c, Cx<P>& d) {
+  Cx<P> s0{P::add(a.re, d.re), P::add(a.im, d.im)};
+  Cx<P> s1{P::add(b.re, c.re), P::add(b.im, c.im)};
+  Cx<P> s2{P::sub(c.im, b.im), P::sub(b.re, c.re)};
+  Cx<P> s3{P::sub(a.re, d.re), P::sub(a.im, d.im)};
+  a = s0; b = s1; c = s2; d = s3;
+}
+template <class P>
+__device__ __forceinline__ void pauli_inv(Cx<P>& z0, Cx<P>& z1, Cx<P>& z2, Cx<P>& z3) {
+  Cx<P> a{P::add(z0.re, z3.re), P::add(z0.im, z3.im)};
+  Cx<P> d{P::sub(z0.re, z3.re), P::sub(z0.im, z3.im)};
+  Cx<P> b{P::add(z1.re, z2.im), P::sub(z1.im, z2.re)};
+  Cx<P> c{P::sub(z1.re, z2.im), P::add(z1.im, z2.re)};
+  z0 = a; z1 = b; z2 = c; z3 = d;
+}
+
+
+// Generic two-qubit map in the two-qubit Pauli basis (coefficients R / 4),
+// all in registers.  Element (ra, ca) of the block, ra = r0 + 2 r1, sits in
+// h[4 ra + ca]; the forward transform runs over bit 0 (r0, c0), then bit 1.
+template <class P>
+__device__ __forceinline__ void body_ptm2(Cx<P> (&h)[16], const double* cf) {
+  using R = typename P::Real;
+#pragma unroll
+  for (int r1 = 0; r1 < 2; ++r1)
+#pragma unroll
+    for (int c1 = 0; c1 < 2; ++c1)
+      pauli_fwd<P>(h[(2 * r1) * 4 + 2 * c1], h[(2 * r1) * 4 + 2 * c1 + 1], h[(2 * r1 + 1) * 4 + 2 * c1],
+                   h[(2 * r1 + 1) * 4 + 2 * c1 + 1]);
+#pragma unroll
+  for (int a0 = 0; a0 < 4; ++a0) {
+    const int o = (a0 >> 1) * 4 + (a0 & 1);
+    pauli_fwd<P>(h[o], h[o + 2], h[o + 8], h[o + 10]);
+  }
+  // h[sidx(a)] now holds s_a, a = a0 + 4 a1
+  constexpr int sidx[16] = {0, 1, 4, 5, 2, 3, 6, 7, 8, 9, 12, 13, 10, 11, 14, 15};
+  Cx<P> z[16];
+#pragma unroll
+  for (int a = 0; a < 16; ++a) {
+    R zr = P::mul(h[sidx[0]].re, P::coef(cf, 16 * a));
+    R zi = P::mul(h[sidx[0]].im, P::coef(cf, 16 * a));
+#pragma unroll
+    for (int b = 1; b < 16; ++b) {
+      zr = P::mac(zr, h[sidx[b]].re, P::coef(cf, 16 * a + b));
+      zi = P::mac(zi, h[sidx[b]].im, P::coef(cf, 16 * a + b));
+    }
+    z[a] = Cx<P>{P::norm(zr), P::norm(zi)};
+  }
+#pragma unroll
+  for (int a = 0; a < 16; ++a) h[sidx[a]] = z[a];
+#pragma unroll
+  for (int a0 = 0; a0 < 4; ++a0) {
+    const int o = (a0 >> 1) * 4 + (a0 & 1);
+    pauli_inv<P>(h[o], h[o + 2], h[o + 8], h[o + 10]);
+  }
+#pragma unroll
+  for (int r1 = 0; r1 < 2; ++r1)
+#pragma unroll
+    for (int c1 = 0; c1 < 2; ++c1)
+      pauli_inv<P>(h[(2 * r1) * 4 + 2 * c1], h[(2 * r1) * 4 + 2 * c1 + 1], h[(2 * r1 + 1) * 4 + 2 * c1],
+                   h[(2 * r1 + 1) * 4 + 2 * c1 + 1]);
+}
+
+// ------------------------------------------------------------------ op drivers
+template <class P>
+__device__ __forceinline__ void apply_1q(typename P::Elem* sm, const SMap& mp, const PassOp& op,
+                                         const double* coef, int rows_log2g, int cols_log2g) {
+  const int ncb_log2 = cols_log2g - 1;
+  const int nb = 1 << (rows_log2g - 1 + ncb_log2);
+  const int rb_bit = 1 << op.rbit[0], cb_bit = 1 << op.cbit[0];
+  const double* cf = coef + op.coef;
+  for (int b = threadIdx.x; b < nb; b += kThreads) {
+    const int cb = b & ((1 << ncb_log2) - 1);
+    const int rb = b >> ncb_log2;
+    const int c0 = ins0i(cb, op.cbit[0]);
+    const int r0 = ins0i(rb, op.rbit[0]);
+    const int i00 = mp.idx(r0, c0), i01 = mp.idx(r0, c0 | cb_bit);
+    const int i10 = mp.idx(r0 | rb_bit, c0), i11 = mp.idx(r0 | rb_bit, c0 | cb_bit);
+    const auto e00 = sm[i00], e01 = sm[i01], e10 = sm[i10], e11 = sm[i11];
+    Cx<P> a{P::re(e00), P::im(e00)}, bb{P::re(e01), P::im(e01)};
+    Cx<P> c{P::re(e10), P::im(e10)}, d{P::re(e11), P::im(e11)};
+    if (op.kind == OP_PTM1_U) body_ptm1_u<P>(a, bb, c, d, cf);
+    else if (op.kind == OP_PTM1_AD) body_ptm1_ad<P>(a, bb, c, d, cf);
+    else body_ptm1<P>(a, bb, c, d, cf);
+    sm[i00] = P::make(a.re, a.im);
+    sm[i01] = P::make(bb.re, bb.im);
+    sm[i10] = P::make(c.re, c.im);
+    sm[i11] = P::make(d.re, d.im);
+  }
+}
+
+template <class P>
+__device__ __forceinline__ void apply_2q(typename P::Elem* sm, const SMap& mp, const PassOp& op,
+                                         const double* coef, int rows_log2g, int cols_log2g) {
+  const int ncb_log2 = cols_log2g - 2;
+  const int nb = 1 << (rows_log2g - 2 + ncb_log2);
+  const double* cf = coef + op.coef;
+  for (int b = threadIdx.x; b < nb; b += kThreads) {
+    const int cb = b & ((1 << ncb_log2) - 1);
+    const int rb = b >> ncb_log2;
+    const int c0 = ins0i(ins0i(cb, op.cbit[0]), op.cbit[1]);
+    const int r0 = ins0i(ins0i(rb, op.rbit[0]), op.rbit[1]);
+    int rows[4], cols[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      rows[a] = r0 | ((a & 1) << op.rbit[0]) | ((a >> 1) << op.rbit[1]);
+      cols[a] = c0 | ((a & 1) << op.cbit[0]) | ((a >> 1) << op.cbit[1]);
+    }
+    int idx[16];
+    Cx<P> h[16];
+#pragma unroll
+    for (int ra = 0; ra < 4; ++ra)
+#pragma unroll
+      for (int ca = 0; ca < 4; ++ca) {
+        idx[4 * ra + ca] = mp.idx(rows[ra], cols[ca]);
+        const auto e = sm[idx[4 * ra + ca]];
+        h[4 * ra + ca] = Cx<P>{P::re(e), P::im(e)};
+      }
+    if (op.kind == OP_U2) {
+      body_u2<P>(h, cf);
+#pragma unroll
+      for (int t = 0; t < 16; ++t) sm[idx[t]] = P::make(h[t].re, h[t].im);
+    } else {
+      body_ptm2<P>(h, cf);
+#pragma unroll
+      for (int t = 0; t < 16; ++t) sm[idx[t]] = P::make(h[t].re, h[t].im);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ the pass kernel
+template <class P, int H>
+__global__ void __launch_bounds__(kThreads, 2)
+pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc d) {
+  using E = typename P::Elem;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E* sm = reinterpret_cast<E*>(smem_raw);
+  constexpr int S = 1 << H;
+  const int m = d.m;
+  const int M = 1 << m;
+  const int rl = d.rows_log2;
+  const int R = 1 << rl;
+  const int slot_log2 = rl + m;
+  const int total = (S * S) << slot_log2;
+  const int64_t tile_elems = int64_t(1) << (2 * m);
+  SMap mp{rl, m, H, P::kSwizzle & (M - 1)};
+  const int rows_log2g = H + rl, cols_log2g = H + m;
+
+  for (int64_t w = blockIdx.x; w < d.n_items; w += gridDim.x) {
+    const int64_t g = w >> d.chunks_log2;
+    const int r0 = int(w & ((int64_t(1) << d.chunks_log2) - 1)) << rl;
+    // chunked passes leave the diagonal groups to pass_kernel_diag and walk
+    // the strictly lower groups only (g = tic (tic - 1) / 2 + tjc, tjc < tic)
+    const int64_t tic = d.skip_diag ? tri_row(g) + 1 : tri_row(g);
+    const int64_t tjc = d.skip_diag ? g - tic * (tic - 1) / 2 : g - tic * (tic + 1) / 2;
+    int64_t bi = tic, bj = tjc;
+#pragma unroll
+    for (int l = 0; l < H; ++l) { bi = ins0(bi, d.hpos[l]); bj = ins0(bj, d.hpos[l]); }
+    const bool diag_group = (tic == tjc);
+
+    // ---- load: global -> shared, upper slots transposed + conjugated
+#pragma unroll 4
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+      const int slot = e >> slot_log2;
+      const int within = e & ((1 << slot_log2) - 1);
+      const int x = slot >> H, y = slot & (S - 1);
+      int64_t ti = bi, tj = bj;
+#pragma unroll
+      for (int l = 0; l < H; ++l) {
+        ti |= int64_t((x >> l) & 1) << d.hpos[l];
+        tj |= int64_t((y >> l) & 1) << d.hpos[l];
+      }
+      if (ti >= tj) {
+        const int r = within >> m, c = within & (M - 1);
+        const int64_t off = (ti * (ti + 1) / 2 + tj) * tile_elems + int64_t(r0 + r) * M + c;
+        sm[(slot << slot_log2) + (r << m) + (c ^ (r & mp.sw))] = st[off];
+      } else {
+        const int r = within & (R - 1), c = within >> rl;
+        const int64_t off = (tj * (tj + 1) / 2 + ti) * tile_elems + int64_t(c) * M + (r0 + r);
+        sm[(slot << slot_log2) + (r << m) + (c ^ (r & mp.sw))] = P::conj(st[off]);
+      }
+    }
+    __syncthreads();
+
+    // ---- the fused ops
+    for (int o = 0; o < d.nops; ++o) {
+      const PassOp& op = d.ops[o];
+      if (op.nq == 1) apply_1q<P>(sm, mp, op, d.coef, rows_log2g, cols_log2g);
+      else apply_2q<P>(sm, mp, op, d.coef, rows_log2g, cols_log2g);
+      __syncthreads();
+    }
+
+    // ---- store: shared -> global, each stored tile exactly once
+#pragma unroll 4
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+      const int slot = e >> slot_log2;
+      const int within = e & ((1 << slot_log2) - 1);
+      const int x = slot >> H, y = slot & (S - 1);
+      int64_t ti = bi, tj = bj;
+#pragma unroll
+      for (int l = 0; l < H; ++l) {
+        ti |= int64_t((x >> l) & 1) << d.hpos[l];
+        tj |= int64_t((y >> l) & 1) << d.hpos[l];
+      }
+      if (ti >= tj) {
+        const int r = within >> m, c = within & (M - 1);
+        const int64_t off = (ti * (ti + 1) / 2 + tj) * tile_elems + int64_t(r0 + r) * M + c;
+        st[off] = sm[(slot << slot_log2) + (r << m) + (c ^ (r & mp.sw))];
+      } else if (!diag_group) {
+        const int r = within & (R - 1), c = within >> rl;
+        const int64_t off = (tj * (tj + 1) / 2 + ti) * tile_elems + int64_t(c) * M + (r0 + r);
+        st[off] = P::conj(sm[(slot << slot_log2) + (r << m) + (c ^ (r & mp.sw))]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+
+// ------------------------------------------------------------------ diagonal groups
+// A diagonal group (ti == tj before the high bits are inserted) is hermitian
+// as a whole: of its 2^h x 2^h slots only the S (S + 1) / 2 with x >= y are
+// stored, and the slot (y, x) above is the conjugate transpose of (x, y).
+// Generalising crossTileDiag (the t_i == t_j subcase of Algorithm 3), this
+// kernel keeps just the stored slots (full tile height) in shared memory and
+// applies every op to one block of each mirror pair {B, B^T}: elements in an
+// upper slot are read and written as conjugates of their stored partner, and
+// inside a diagonal slot both (r, c) and (c, r) are written.  Used for the
+// passes whose tile groups do not fit shared memory at full height.
+struct DMap {
+  int m, sw;
+  __device__ __forceinline__ int at(int s, int r, int c) const { return (((s << m) | r) << m) | (c ^ (r & sw)); }
+};
+
+template <class P>
+__device__ __forceinline__ Cx<P> dread(const typename P::Elem* sm, const DMap& mp, int li, int lj) {
+  const int M1 = (1 << mp.m) - 1;
+  const int x = li >> mp.m, r = li & M1, y = lj >> mp.m, c = lj & M1;
+  if (x >= y) {
+    const auto e = sm[mp.at(x * (x + 1) / 2 + y, r, c)];
+    return Cx<P>{P::re(e), P::im(e)};
+  }
+  const auto e = sm[mp.at(y * (y + 1) / 2 + x, c, r)];
+  return Cx<P>{P::re(e), P::neg(P::im(e))};
+}
+
+template <class P>
+__device__ __forceinline__ void dwrite(typename P::Elem* sm, const DMap& mp, int li, int lj, const Cx<P>& v) {
+  const int M1 = (1 << mp.m) - 1;
+  const int x = li >> mp.m, r = li & M1, y = lj >> mp.m, c = lj & M1;
+  if (x > y) {
+    sm[mp.at(x * (x + 1) / 2 + y, r, c)] = P::make(v.re, v.im);
+  } else if (x == y) {
+    sm[mp.at(x * (x + 1) / 2 + x, r, c)] = P::make(v.re, v.im);
+    if (r != c) sm[mp.at(x * (x + 1) / 2 + x, c, r)] = P::make(v.re, P::neg(v.im));
+  } else {
+    sm[mp.at(y * (y + 1) / 2 + x, c, r)] = P::make(v.re, P::neg(v.im));
+  }
+}
+
+template <class P>
+__device__ __forceinline__ void diag_apply(typename P::Elem* sm, const DMap& mp, const PassOp& op,
+                                           const double* coef, int log2g) {
+  // blocks (i, j), i >= j, of the (2^log2g / 2^k)^2 block grid; rows and
+  // columns share the bit positions op.cbit (no chunking here)
+  const int k = op.nq;
+  const int nb1 = 1 << (log2g - k);
+  const int nblk = nb1 * (nb1 + 1) / 2;
+  const double* cf = coef + op.coef;
+  for (int b = threadIdx.x; b < nblk; b += kThreads) {
+    const int i = int(tri_row(b)), j = b - i * (i + 1) / 2;
+    if (k == 1) {
+      const int rb = ins0i(i, op.cbit[0]), cb = ins0i(j, op.cbit[0]), bit = 1 << op.cbit[0];
+      Cx<P> a = dread<P>(sm, mp, rb, cb), bb = dread<P>(sm, mp, rb, cb | bit);
+      Cx<P> c = dread<P>(sm, mp, rb | bit, cb), d = dread<P>(sm, mp, rb | bit, cb | bit);
+      if (op.kind == OP_PTM1_U) body_ptm1_u<P>(a, bb, c, d, cf);
+      else if (op.kind == OP_PTM1_AD) body_ptm1_ad<P>(a, bb, c, d, cf);
+      else body_ptm1<P>(a, bb, c, d, cf);
+      dwrite<P>(sm, mp, rb, cb, a);
+      dwrite<P>(sm, mp, rb, cb | bit, bb);
+      dwrite<P>(sm, mp, rb | bit, cb, c);
+      dwrite<P>(sm, mp, rb | bit, cb | bit, d);
+    } else {
+      const int rb = ins0i(ins0i(i, op.cbit[0]), op.cbit[1]);
+      const int cb = ins0i(ins0i(j, op.cbit[0]), op.cbit[1]);
+      int rows[4], cols[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        rows[a] = rb | ((a & 1) << op.cbit[0]) | ((a >> 1) << op.cbit[1]);
+        cols[a] = cb | ((a & 1) << op.cbit[0]) | ((a >> 1) << op.cbit[1]);
+      }
+      Cx<P> h[16];
+#pragma unroll
+      for (int ra = 0; ra < 4; ++ra)
+#pragma unroll
+        for (int ca = 0; ca < 4; ++ca) h[4 * ra + ca] = dread<P>(sm, mp, rows[ra], cols[ca]);
+      if (op.kind == OP_U2) body_u2<P>(h, cf);
+      else body_ptm2<P>(h, cf);
+#pragma unroll
+      for (int ra = 0; ra < 4; ++ra)
+#pragma unroll
+        for (int ca = 0; ca < 4; ++ca) dwrite<P>(sm, mp, rows[ra], cols[ca], h[4 * ra + ca]);
+    }
+  }
+}
+
+template <class P, int H>
+__global__ void __launch_bounds__(kThreads, 1)
+pass_kernel_diag(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto* sm = reinterpret_cast<typename P::Elem*>(smem_raw);
+  constexpr int S = 1 << H;
+  constexpr int NS = S * (S + 1) / 2;
+  const int m = d.m;
+  const int M = 1 << m;
+  const int64_t tile_elems = int64_t(1) << (2 * m);
+  const DMap mp{m, P::kSwizzle & (M - 1)};
+  for (int64_t t = blockIdx.x; t < d.nt_c; t += gridDim.x) {
+    int64_t b = t;
+#pragma unroll
+    for (int l = 0; l < H; ++l) b = ins0(b, d.hpos[l]);
+    for (int pass = 0; pass < 2; ++pass) {
+      // pass 0 loads the stored slots, pass 1 (after the ops) stores them back
+      if (pass == 1) {
+        for (int o = 0; o < d.nops; ++o) {
+          diag_apply<P>(sm, mp, d.ops[o], d.coef, H + m);
+          __syncthreads();
+        }
+      }
+#pragma unroll 4
+      for (int e = threadIdx.x; e < (NS << (2 * m)); e += kThreads) {
+        const int s = e >> (2 * m);
+        const int w = e & ((1 << (2 * m)) - 1);
+        const int x = int(tri_row(s)), y = s - x * (x + 1) / 2;
+        int64_t ti = b, tj = b;
+#pragma unroll
+        for (int l = 0; l < H; ++l) {
+          ti |= int64_t((x >> l) & 1) << d.hpos[l];
+          tj |= int64_t((y >> l) & 1) << d.hpos[l];
+        }
+        const int r = w >> m, c = w & (M - 1);
+        const int64_t off = (ti * (ti + 1) / 2 + tj) * tile_elems + w;
+        if (pass == 0) sm[mp.at(s, r, c)] = st[off];
+        else st[off] = sm[mp.at(s, r, c)];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Occupancy-sized persistent grid for one kernel instantiation (cached per device and smem size).
+struct LaunchCache {
+  int dev = -1;
+  size_t smem = 0;
+  int blocks = 0;
+  int sms = 0;
+};
+
+template <class E>
+cudaError_t launch_one(void (*kfn)(E*, PassDesc), LaunchCache& lc, size_t smem, int64_t items, void* state,
+                       const PassDesc& d, cudaStream_t s) {
+  if (items <= 0) return cudaSuccess;
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (lc.dev != dev || lc.smem != smem) {
+    err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (err != cudaSuccess) return err;
+    int nb = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kThreads, smem);
+    if (err != cudaSuccess) return err;
+    err = cudaDeviceGetAttribute(&lc.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return err;
+    lc.dev = dev;
+    lc.smem = smem;
+    lc.blocks = nb > 0 ? nb : 1;
+  }
+  int64_t grid = int64_t(lc.blocks) * lc.sms;
+  if (grid > items) grid = items;
+  kfn<<<dim3(unsigned(grid)), dim3(kThreads), smem, s>>>(reinterpret_cast<E*>(state), d);
+  return cudaGetLastError();
+}
+
+template <class P, int H>
+cudaError_t launch_t(void* state, const PassDesc& d, cudaStream_t s, int* launches) {
+  using E = typename P::Elem;
+  static thread_local LaunchCache main_cache, diag_cache;
+  const size_t smem = sizeof(E) * (size_t(1) << (2 * H + d.rows_log2 + d.m));
+  cudaError_t err = launch_one<E>(pass_kernel<P, H>, main_cache, smem, d.n_items, state, d, s);
+  if (err != cudaSuccess) return err;
+  int n = d.n_items > 0 ? 1 : 0;
+  if (d.skip_diag) {
+    const size_t dsmem = sizeof(E) * size_t((1 << H) * ((1 << H) + 1) / 2) * (size_t(1) << (2 * d.m));
+    err = launch_one<E>(pass_kernel_diag<P, H>, diag_cache, dsmem, d.nt_c, state, d, s);
+    if (err != cudaSuccess) return err;
+    n += 1;
+  }
+  if (launches) *launches = n;
+  return cudaSuccess;
+}
+template <class P>
+cudaError_t launch_p(void* state, const PassDesc& d, cudaStream_t s, int* launches) {
+  switch (d.h) {
+    case 0: return launch_t<P, 0>(state, d, s, launches);
+    case 1: return launch_t<P, 1>(state, d, s, launches);
+    case 2: return launch_t<P, 2>(state, d, s, launches);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_pass(int dtype, void* state, const PassDesc& d, cudaStream_t s, int* launches) {
+  if (launches) *launches = 0;
+  switch (dtype) {
+    case DT_C128: return launch_p<PolF64>(state, d, s, launches);
+    case DT_C64: return launch_p<PolF32>(state, d, s, launches);
+    case DT_DF64: return launch_p<PolDF64>(state, d, s, launches);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace orkan

@@ -1,0 +1,90 @@
+"""The C-ABI library without a GPU: it loads, exports every entry point that
+include/orkan.h declares, and its host-only functions (layout, bit insertion,
+Pauli transfer matrices) agree with the oracle."""
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import dense as D
+from oracle import tiled as T
+from paper_2604_15765_gb300 import orkan as ok
+from workloads import synth as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "orkan.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(orkan_\w+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_functions()
+    assert len(names) >= 30
+    for name in names:
+        assert hasattr(ok._lib, name), name
+        assert name in ok.EXPORTED, f"binding lacks {name}"
+
+
+def test_bytes_follow_table1_formula():
+    for n in range(1, 20):
+        for m in (2, 3, 4, 5):
+            assert ok.orkan_bytes(n, ok.ORKAN_C128, m) == T.stored_bytes(n, m, 16)
+            assert ok.orkan_bytes(n, ok.ORKAN_DF64, m) == T.stored_bytes(n, m, 16)
+            assert ok.orkan_bytes(n, ok.ORKAN_C64, m) == T.stored_bytes(n, m, 8)
+            assert ok.orkan_num_tiles(n, m) == T.num_tiles(n, m)
+    assert ok.orkan_bytes(5, ok.ORKAN_C128, 0) == 16384          # default m = 5
+    assert ok.orkan_bytes(0, ok.ORKAN_C128, 5) == 0               # invalid n
+    assert ok.orkan_bytes(4, 7, 5) == 0                           # invalid dtype
+    assert ok.orkan_bytes(4, ok.ORKAN_C128, 6) == 0               # tile too large (m <= 5)
+
+
+@pytest.mark.parametrize("n,m", [(1, 5), (3, 2), (5, 5), (6, 2), (7, 3), (8, 5)])
+def test_element_offset_matches_oracle(n, m):
+    for i in range(1 << n):
+        for j in range(1 << n):
+            assert ok.orkan_element_offset(n, m, i, j) == T.element_offset(i, j, n, m)
+    assert ok.orkan_element_offset(n, m, 1 << n, 0)[0] == -1
+
+
+def test_insert_bits_matches_oracle():
+    for n in range(1, 7):
+        for k in range(1, min(3, n) + 1):
+            for A in itertools.combinations(range(n), k):
+                for s in range(1 << (n - k)):
+                    for a in range(1 << k):
+                        assert ok.orkan_insert_bits(s, a, A) == T.insert_bits(s, a, A)
+
+
+def _pauli(a, k):
+    P = np.ones((1, 1), dtype=np.complex128)
+    for l in reversed(range(k)):
+        P = np.kron(P, [D.I2, D.X, D.Y, D.Z][(a >> (2 * l)) & 3])
+    return P
+
+
+@pytest.mark.parametrize("k,r", [(1, 1), (1, 2), (1, 4), (2, 1), (2, 3)])
+def test_ptm_reproduces_the_kraus_map(k, r):
+    rng = S.rng_for(500 + 10 * k + r)
+    d = 1 << k
+    kraus = [rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d)) for _ in range(r)]
+    B = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+    for adjoint in (False, True):
+        R = ok.orkan_ptm(k, kraus, adjoint)
+        expect = D.apply_kraus(B, kraus, list(range(k)), "heisenberg" if adjoint else "schrodinger")
+        z = np.array([np.trace(_pauli(b, k) @ B) / d for b in range(4 ** k)])
+        got = sum((R[a] @ z) * _pauli(a, k) for a in range(4 ** k))
+        assert np.max(np.abs(got - expect)) < 1e-12
+
+
+def test_alloc_without_gpu_reports_no_device():
+    from conftest import gpu_available
+    if gpu_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(ok.OrkanError) as e:
+        ok.orkan_alloc(4, ok.ORKAN_C128, 5)
+    assert e.value.status == ok.ORKAN_ENODEV

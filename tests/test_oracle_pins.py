@@ -234,7 +234,7 @@ def test_bell_amplitude_damping():
         expect[2, 2] = g / 2
         expect[3, 3] = (1 - g) / 2
         expect[0, 3] = expect[3, 0] = np.sqrt(1 - g) / 2
-        assert np.max(np.abs(rho - expect)) < 1e-16
+        assert np.max(np.abs(rho - expect)) <= 2.3e-16   # two roundings of 0.5-sized values
 
 
 def test_ghz_depolarized():
@@ -356,6 +356,17 @@ def test_pauli_expectations_on_basis_and_ghz():
     assert D.expect_pauli(np.eye(1 << n) / (1 << n), "XYZI") == 0
 
 
+def test_pauli_y_eigenstate():
+    """|+i> = (|0> + i|1>)/sqrt2 has <Y> = +1; on qubit 1 of a 2-qubit
+    product with |0> on qubit 0, <ZY> (char 0 = Z on qubit 0) = +1."""
+    v = np.array([1, 1j]) / np.sqrt(2)
+    assert D.expect_pauli(np.outer(v, v.conj()), "Y") == pytest.approx(1.0)
+    w = np.kron(v, np.array([1, 0]))   # qubit 1 in |+i>, qubit 0 in |0>
+    rho = np.outer(w, w.conj())
+    assert D.expect_pauli(rho, "ZY") == pytest.approx(1.0)
+    assert D.expect_pauli(rho, "YZ") == pytest.approx(0.0)
+
+
 def test_tiled_mean_value_equals_trace():
     rng = S.rng_for(400)
     for n, m in ((3, 1), (5, 2), (6, 5), (2, 5), (6, 3)):
@@ -394,14 +405,30 @@ def test_planted_mistakes_are_caught(monkeypatch):
     with monkeypatch.context() as mp:
         mp.setattr(D, "embed", lambda L, q, n, sparse=None: orig_embed(np.asarray(L).T, q, n, sparse))
         with pytest.raises(AssertionError):
-            test_cnot_on_basis_states()
+            test_bell_amplitude_damping()
     # 4) a wrong sign in Y
     with monkeypatch.context() as mp:
         mp.setattr(D, "PAULI", dict(D.PAULI, Y=-D.Y))
         with pytest.raises(AssertionError):
-            test_bell_depolarized_is_werner()
+            test_pauli_y_eigenstate()
     # 5) swapped qubit order in the Kronecker product
     with monkeypatch.context() as mp:
         mp.setattr(D, "embed", lambda L, q, n, sparse=None: orig_embed(L, [n - 1 - x for x in q], n, sparse))
         with pytest.raises(AssertionError):
             test_bell_amplitude_damping()
+
+
+def test_factored_kraus_matches_dense():
+    """Eq. (1) on H = sum_v v v^dagger through the factors equals the dense map,
+    and factored_elements reads H's entries (used for sampled checks at large n)."""
+    rng = S.rng_for(600)
+    n = 5
+    vecs = [S.haar_state_vector(rng, 1 << n) * w for w in (0.7, 0.5, 0.2)]
+    H = sum(np.outer(v, v.conj()) for v in vecs)
+    for kraus, qubits in ((D.depolarizing_kraus(0.2), [3]), ([S.haar_unitary(rng, 4)], [4, 1]),
+                          (D.amplitude_damping_kraus(0.3), [0])):
+        out = D.apply_kraus_to_factors(vecs, kraus, qubits, n)
+        dense = sum(np.outer(v, v.conj()) for v in out)
+        assert np.max(np.abs(dense - D.apply_kraus(H, kraus, qubits))) < 1e-15
+        rows, cols = rng.integers(0, 1 << n, 50), rng.integers(0, 1 << n, 50)
+        assert np.max(np.abs(D.factored_elements(out, rows, cols) - dense[rows, cols])) < 1e-15
