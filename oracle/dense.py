@@ -296,3 +296,29 @@ def trace_distance(A, B) -> float:
     D = np.asarray(A) - np.asarray(B)
     D = 0.5 * (D + D.conj().T)
     return float(0.5 * np.sum(np.abs(np.linalg.eigvalsh(D))))
+
+
+# --------------------------------------------------------------------------
+# Eq. (1) on a factored operator (for sampled checks at large n)
+# --------------------------------------------------------------------------
+def apply_kraus_to_factors(vectors, kraus, qubits, n):
+    """For H = sum_v v v^dagger, Eq. (1) gives Phi(H) = sum_alpha sum_v
+    (K_alpha v)(K_alpha v)^dagger; return the list of all K_alpha v.  Each
+    K_alpha is the same explicit (sparse above DENSE_MAX_N) Kronecker
+    embedding used by :func:`apply_kraus`."""
+    out = []
+    for L in kraus:
+        K = embed(L, qubits, n)
+        for v in vectors:
+            out.append(np.asarray(K @ v).reshape(-1))
+    return out
+
+
+def factored_elements(vectors, rows, cols):
+    """H[rows[t], cols[t]] of H = sum_v v v^dagger."""
+    rows = np.asarray(rows)
+    cols = np.asarray(cols)
+    out = np.zeros(rows.shape, dtype=np.complex128)
+    for v in vectors:
+        out += v[rows] * np.conj(v[cols])
+    return out
