@@ -224,6 +224,41 @@ int orkan_set_timing(orkan_h h, int enable);
  * recorded since the last call, their count, and reset. */
 int orkan_pass_time(orkan_h h, double *ms, int64_t *count);
 
+/* ------------------------------------------------------------------ allocation-free readout
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * must not allocate device memory themselves -- e.g. code that runs while a
+ * host framework owns all device memory through its own pool and forbids side
+ * allocations, serving loops where an allocation could synchronise the device
+ * or fail under fragmentation, or plugins that are only handed the device
+ * pointer of a tiled operator.
+ *
+ * tr(P_s H) for count Pauli strings P_s (count * n characters of "IXYZ" back
+ * to back, character l on qubit l), read from the tiled array at dev_state
+ * (caller-owned device memory: n qubits, dtype, tile_log2 as for orkan_alloc,
+ * layout of Sec. III-B, with any pending fused ops of its handle already
+ * flushed).  The results go to the host array out[count].  Work is issued on
+ * cuda_stream (NULL = legacy default stream) and the call returns after it.
+ *
+ * Scratch: no cudaMalloc / cudaFree or other allocating routine is called.  The
+ * partial sums live in one fixed, file-scope device array of
+ * ORKAN_NOALLOC_MAX_STRINGS x 608 x 2 + 2 x ORKAN_NOALLOC_MAX_STRINGS doubles
+ * (about 609 KB), which every GPU that loads the library holds until the
+ * process exits.  count above ORKAN_NOALLOC_MAX_STRINGS is rejected with
+ * ORKAN_EINVAL and a message naming the limit.  The array is shared by every
+ * call and keeps the last call's contents; each call rewrites every entry it
+ * reads, so nothing needs clearing, but calls whose work overlaps on the GPU
+ * (other host threads, other streams) race on it and must be serialised by the
+ * caller.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) once, with that device current; make that first call
+ * before any stream capture.
+ *
+ * Results equal orkan_expect_pauli's bit for bit (same reduction order).
+ * Errors: EINVAL (null pointers, bad n / dtype / tile_log2, count out of
+ * range, bad character), ECUDA. */
+#define ORKAN_NOALLOC_MAX_STRINGS 64
+int orkan_expect_paulis_noalloc(const void *dev_state, int n, int dtype, int tile_log2, int count,
+                                const char *paulis, double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liborkan_gb300.so")
-SOURCES = ["pass_kernels.cu", "aux_kernels.cu", "orkan_api.cpp"]
+SOURCES = ["pass_kernels.cu", "aux_kernels.cu", "orkan_api.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

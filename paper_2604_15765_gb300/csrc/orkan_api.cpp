@@ -505,6 +505,8 @@ int common_alloc(int n, int dtype, int tile_log2, void* dev_ptr, size_t bytes, o
 
 }  // namespace
 
+void orkan::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 // =================================================================== C ABI
 extern "C" {
 

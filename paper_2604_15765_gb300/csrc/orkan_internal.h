@@ -64,6 +64,9 @@ struct PassDesc {
   double coef[kMaxCoef];   // F64: double; DF64: float2 (hi, lo); C64: float in the low half
 };
 
+// Record the message that orkan_last_error() returns on the calling thread.
+void set_last_error(const char* msg);
+
 // Launchers (pass_kernels.cu).  Return cudaSuccess or the launch error;
 // *launches receives the number of kernels launched (1 or 2).
 cudaError_t launch_pass(int dtype, void* state, const PassDesc& d, cudaStream_t s, int* launches);

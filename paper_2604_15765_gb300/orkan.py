@@ -74,6 +74,8 @@ _SIGS = {
     "orkan_stats": (C.c_int, [_h, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)]),
     "orkan_set_timing": (C.c_int, [_h, C.c_int]),
     "orkan_pass_time": (C.c_int, [_h, _pd, C.POINTER(_i64)]),
+    "orkan_expect_paulis_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_char_p, _pd,
+                                              C.c_void_p]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -282,6 +284,19 @@ def orkan_stats(h):
 
 def orkan_set_timing(h, enable: bool):
     _check(_lib.orkan_set_timing(h, int(enable)), "orkan_set_timing")
+
+
+ORKAN_NOALLOC_MAX_STRINGS = 64
+
+
+def orkan_expect_paulis_noalloc(dev_state: int, n: int, dtype: int, tile_log2: int, paulis, stream_ptr=None):
+    """tr(P_s H) for up to ORKAN_NOALLOC_MAX_STRINGS Pauli strings, read from a
+    caller-owned tiled device array, with no device allocation (see orkan.h)."""
+    out = np.zeros(len(paulis))
+    s = "".join(paulis).encode()
+    _check(_lib.orkan_expect_paulis_noalloc(C.c_void_p(dev_state), n, dtype, tile_log2, len(paulis), s, _dptr(out),
+                                            C.c_void_p(stream_ptr or 0)), "orkan_expect_paulis_noalloc")
+    return out
 
 
 def orkan_pass_time(h):
