@@ -54,6 +54,8 @@ def parse_args(argv=None):
     p.add_argument("--no-variants", action="store_true", help="skip the c128 / c64 / unfused comparison runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=20.0)
+    p.add_argument("--op-class", default=None,
+                   help="time only single-op passes of one class (u1_in, u2_in_cross, ...) and print their GB/s")
     return p.parse_args(argv)
 
 
@@ -233,6 +235,50 @@ class Runner:
         self.ok.orkan_free(self.O)
 
 
+def per_op_table(ok, wl, n, m, dtypes, stream, torch, reps=4, only=None):
+    """HBM GB/s of single-op passes (fusion 1, no composition) per op class,
+    in-tile (target 1 < m) and cross-tile (target n-2 >= m), per dtype: the
+    per-pass view of the sweep (2 x stored bytes / pass time)."""
+    from workloads import synth as S
+    rng = S.rng_for(S.BASE_SEED + 11)
+    U1, U2 = S.haar_unitary(rng, 2), S.haar_unitary(rng, 4)
+    lo, hi = 1, n - 2
+    classes = {
+        "u1_in": lambda h: ok.orkan_apply_unitary(h, [lo], U1),
+        "u1_cross": lambda h: ok.orkan_apply_unitary(h, [hi], U1),
+        "depol_in": lambda h: ok.orkan_depolarize(h, lo, 0.1),
+        "depol_cross": lambda h: ok.orkan_depolarize(h, hi, 0.1),
+        "ampdamp_in": lambda h: ok.orkan_amplitude_damp(h, lo, 0.05),
+        "ampdamp_cross": lambda h: ok.orkan_amplitude_damp(h, hi, 0.05),
+        "u2_in_in": lambda h: ok.orkan_apply_unitary(h, [lo, lo + 1], U2),
+        "u2_in_cross": lambda h: ok.orkan_apply_unitary(h, [lo, hi], U2),
+        "u2_cross_cross": lambda h: ok.orkan_apply_unitary(h, [hi - 1, hi], U2),
+    }
+    if only is not None:
+        classes = {only: classes[only]}
+    out = {}
+    for dt in dtypes:
+        h = ok.orkan_alloc(n, DTYPE_NAMES[dt], m)
+        ok.orkan_set_stream(h, stream)
+        ok.orkan_set_fusion(h, 1, False)
+        ok.orkan_init_state(h, ok.ORKAN_INIT_PURE, wl["psi"])
+        nbytes = 2 * ok.orkan_bytes(n, DTYPE_NAMES[dt], m)
+        row = {}
+        for name, fn in classes.items():
+            fn(h)
+            ok.orkan_sync(h)
+            ok.orkan_set_timing(h, True)
+            ok.orkan_pass_time(h)
+            for _ in range(reps):
+                fn(h)
+            ms, cnt = ok.orkan_pass_time(h)
+            ok.orkan_set_timing(h, False)
+            row[name] = round(nbytes / (ms / cnt * 1e-3) / 1e9, 1)
+        out[dt] = row
+        ok.orkan_free(h)
+    return out
+
+
 def time_steps(runner, steps, warmup, torch):
     for _ in range(warmup):
         runner.step()
@@ -256,6 +302,12 @@ def time_steps(runner, steps, warmup, torch):
     return ms, pass_ms, pass_cnt, runner.launches() - l0
 
 
+def _sample_ops(wl):
+    """The CPU sample: the sweep's single-qubit Haar unitaries (the cheapest
+    op class for the dense oracle, two N x N products each)."""
+    return [op for op in wl["ops"] if op["kind"] == "unitary" and len(op["qubits"]) == 1]
+
+
 def cpu_baseline(wl, n, seconds):
     """The oracle as it stands, on the same sweep at the same n, until the time
     budget is spent (at least one op); returns ops/s and the sample."""
@@ -265,26 +317,27 @@ def cpu_baseline(wl, n, seconds):
     rho = np.outer(psi, psi.conj())
     t0 = time.perf_counter()
     done = 0
-    for op in wl["ops"]:
+    for op in _sample_ops(wl):
         rho, _ = D.apply_op(rho, op)
         done += 1
         if time.perf_counter() - t0 > seconds:
             break
     dt = time.perf_counter() - t0
     return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {done} ops of the n={n} sweep on a dense complex128 rho (scipy.sparse Kronecker "
-                      f"K, single-threaded), {dt:.1f} s"}
+            "sample": f"{done} single-qubit Haar unitaries of the n={n} sweep on a dense complex128 rho "
+                      f"(scipy.sparse Kronecker K, single-threaded), {dt:.1f} s"}
 
 
 def run_reference(args):
-    """--impl reference: the oracle, timed as it stands on the host cores."""
+    """--impl reference: the oracle, timed as it stands on the host cores,
+    one single-qubit unitary of the n-qubit sweep per step."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
     import numpy as np
     from oracle import dense as D
     wl = make_workload(args.n)
-    ops = wl["ops"]
+    ops = _sample_ops(wl)
     psi = wl["psi"]
     rho = np.outer(psi, psi.conj())
     k = 0
@@ -301,9 +354,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": f"per-op sweep n={args.n} (one k-local op of the sweep per step)", "n": args.n},
+        "config": {"workload": f"per-op sweep n={args.n}: one single-qubit Haar unitary of the sweep per step "
+                               f"(dense complex128 oracle)", "n": args.n},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} ops of the n={args.n} sweep, one per step, dense complex128 oracle"},
+                         "sample": f"{args.steps} single-qubit Haar unitaries of the n={args.n} sweep, one per step"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -330,6 +384,10 @@ def main(argv=None):
     n, m = args.n, args.tile_log2
     wl = make_workload(n)
     stream = torch.cuda.current_stream().cuda_stream
+    if args.op_class:
+        tab = per_op_table(ok, wl, n, m, (args.dtype,), stream, torch, reps=args.steps, only=args.op_class)
+        print(json.dumps({"op_class": args.op_class, "dtype": args.dtype, "n": n, "pass_GBps": tab[args.dtype]}))
+        return 0
     compose = not args.no_compose
     runner = Runner(ok, circuit, wl, n, m, args.dtype, args.fusion, compose, stream)
 
@@ -395,6 +453,10 @@ def main(argv=None):
                               "avg_pass_GBps": round(2.0 * r.bytes / (vpass / max(vcnt, 1) * 1e-3) / 1e9, 1)}
             r.free()
 
+    per_op = None
+    if not args.no_variants and world == 1:
+        per_op = per_op_table(ok, wl, n, m, ("df64", "c128", "c64"), stream, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, n, args.cpu_seconds)
@@ -418,6 +480,7 @@ def main(argv=None):
             "gpu_launches": launches,
             "clocks": clocks,
             "variants": variants,
+            "per_op_pass_GBps": per_op,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

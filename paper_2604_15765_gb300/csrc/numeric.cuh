@@ -23,7 +23,13 @@ struct PolF64 {
   using Real = double;
   using Coef = double;
   static constexpr int kSwizzle = 7;  // 16-byte elements: 8 per 128-byte bank line
+  static constexpr int kSwShift = 0;  // swizzle granule = 1 element (16 B)
   static __device__ __forceinline__ Coef coef(const double* c, int i) { return c[i]; }
+  // conjugate when t == 1, by flipping the sign bit (no FP64 instruction)
+  static __device__ __forceinline__ Elem conj_if(Elem e, unsigned t) {
+    e.y = __hiloint2double(__double2hiint(e.y) ^ int(t << 31), __double2loint(e.y));
+    return e;
+  }
   static __device__ __forceinline__ Real re(const Elem& e) { return e.x; }
   static __device__ __forceinline__ Real im(const Elem& e) { return e.y; }
   static __device__ __forceinline__ Elem make(Real r, Real i) { return make_double2(r, i); }
@@ -44,8 +50,13 @@ struct PolF32 {
   using Real = float;
   using Coef = float;
   static constexpr int kSwizzle = 15;  // 8-byte elements: 16 per 128-byte bank line
+  static constexpr int kSwShift = 1;   // swizzle granule = 2 elements (16 B, one cp.async)
   static __device__ __forceinline__ Coef coef(const double* c, int i) {
     return reinterpret_cast<const float*>(c)[2 * i];
+  }
+  static __device__ __forceinline__ Elem conj_if(Elem e, unsigned t) {
+    e.y = __int_as_float(__float_as_int(e.y) ^ int(t << 31));
+    return e;
   }
   static __device__ __forceinline__ Real re(const Elem& e) { return e.x; }
   static __device__ __forceinline__ Real im(const Elem& e) { return e.y; }
@@ -86,8 +97,14 @@ struct PolDF64 {
   using Real = DF;
   using Coef = float2;   // (hi, lo) split of an FP64 coefficient, made on the host
   static constexpr int kSwizzle = 7;
+  static constexpr int kSwShift = 0;
   static __device__ __forceinline__ Coef coef(const double* c, int i) {
     return reinterpret_cast<const float2*>(c)[i];
+  }
+  static __device__ __forceinline__ Elem conj_if(Elem e, unsigned t) {
+    e.z = __int_as_float(__float_as_int(e.z) ^ int(t << 31));
+    e.w = __int_as_float(__float_as_int(e.w) ^ int(t << 31));
+    return e;
   }
   static __device__ __forceinline__ Real re(const Elem& e) { return {e.x, e.y}; }
   static __device__ __forceinline__ Real im(const Elem& e) { return {e.z, e.w}; }

@@ -38,15 +38,43 @@ __device__ __forceinline__ int ins0i(int x, int p) {
   return ((x >> p) << (p + 1)) | low;
 }
 
-struct SMap {
+// Group layout in shared memory.  Logical element (li, lj) of the
+// (2^H R) x (2^H M) group, li = x R + r, lj = y M + c, lives in slot (x, y)
+// at row r; the element (16-byte granule) index inside a row is
+// XOR-swizzled with the row so that row-wise and column-wise walks hit
+// distinct banks:
+//   idx = ((x 2^H + y) R + r) M + (c ^ ((r & sw) << SH)).
+// Slots whose tile lies in the upper triangle are loaded already transposed
+// and conjugated, so every op sees plain logical elements.
+template <class P>
+struct GMap {
   int rl, m, H, sw;
   __device__ __forceinline__ int idx(int li, int lj) const {
     const int x = li >> rl, r = li & ((1 << rl) - 1);
     const int y = lj >> m, c = lj & ((1 << m) - 1);
-    const int slot = (x << H) | y;
-    return (((slot << rl) | r) << m) | (c ^ (r & sw));
+    return ((((x << H) | y) << rl | r) << m) + (c ^ ((r & sw) << P::kSwShift));
+  }
+  // index of the partner whose row (or column) index has bit `pos` set, as
+  // idx' = (idx + add) ^ xr, for an element whose index has that bit clear
+  __device__ __forceinline__ void row_delta(int pos, int& add, int& xr) const {
+    if (pos < rl) { add = (1 << pos) << m; xr = ((1 << pos) & sw) << P::kSwShift; }
+    else { add = (1 << (pos - rl)) << (H + rl + m); xr = 0; }
+  }
+  __device__ __forceinline__ void col_delta(int pos, int& add, int& xr) const {
+    if (pos < m) { add = 0; xr = 1 << pos; }
+    else { add = (1 << (pos - m)) << (rl + m); xr = 0; }
   }
 };
+
+template <class P>
+__device__ __forceinline__ Cx<P> ld(const typename P::Elem* sm, int i) {
+  const auto e = sm[i];
+  return Cx<P>{P::re(e), P::im(e)};
+}
+template <class P>
+__device__ __forceinline__ void st(typename P::Elem* sm, int i, const Cx<P>& v) {
+  sm[i] = P::make(v.re, v.im);
+}
 
 // ------------------------------------------------------------------ op bodies
 // A 2x2 block [[a, b], [c, d]] in Pauli coordinates s_k = 2 z_k:
@@ -246,161 +274,307 @@ __device__ __forceinline__ void body_ptm2(Cx<P> (&h)[16], const double* cf) {
                    h[(2 * r1 + 1) * 4 + 2 * c1 + 1]);
 }
 
+// out[i] = sum_k A[i][k] in[k] for the 4x4 complex A = V (CONJ = false) or
+// conj(V) (CONJ = true); V row-major, re/im interleaved in the coefficients.
+template <class P, bool CONJ>
+__device__ __forceinline__ void matvec4(const Cx<P> (&in)[4], Cx<P> (&out)[4], const double* cf) {
+  using R = typename P::Real;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    R accr, acci;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const auto ar = P::coef(cf, 2 * (4 * i + k)), ai = P::coef(cf, 2 * (4 * i + k) + 1);
+      // V:       re += ar xr - ai xi,  im += ar xi + ai xr
+      // conj(V): re += ar xr + ai xi,  im += ar xi - ai xr
+      const R xr = in[k].re, xi = in[k].im;
+      if (k == 0) {
+        accr = P::mul(xr, ar);
+        acci = P::mul(xi, ar);
+      } else {
+        accr = P::mac(accr, xr, ar);
+        acci = P::mac(acci, xi, ar);
+      }
+      accr = P::mac(accr, CONJ ? xi : P::neg(xi), ai);
+      acci = P::mac(acci, CONJ ? P::neg(xr) : xr, ai);
+    }
+    out[i] = Cx<P>{P::norm(accr), P::norm(acci)};
+  }
+}
+
 // ------------------------------------------------------------------ op drivers
-template <class P>
-__device__ __forceinline__ void apply_1q(typename P::Elem* sm, const SMap& mp, const PassOp& op,
+template <class P, int NT>
+__device__ __forceinline__ void apply_1q(typename P::Elem* sm, const GMap<P>& gm, const PassOp& op,
                                          const double* coef, int rows_log2g, int cols_log2g) {
   const int ncb_log2 = cols_log2g - 1;
   const int nb = 1 << (rows_log2g - 1 + ncb_log2);
-  const int rb_bit = 1 << op.rbit[0], cb_bit = 1 << op.cbit[0];
+  int ra, rx, ca, cx;
+  gm.row_delta(op.rbit[0], ra, rx);
+  gm.col_delta(op.cbit[0], ca, cx);
   const double* cf = coef + op.coef;
-  for (int b = threadIdx.x; b < nb; b += kThreads) {
-    const int cb = b & ((1 << ncb_log2) - 1);
-    const int rb = b >> ncb_log2;
-    const int c0 = ins0i(cb, op.cbit[0]);
-    const int r0 = ins0i(rb, op.rbit[0]);
-    const int i00 = mp.idx(r0, c0), i01 = mp.idx(r0, c0 | cb_bit);
-    const int i10 = mp.idx(r0 | rb_bit, c0), i11 = mp.idx(r0 | rb_bit, c0 | cb_bit);
-    const auto e00 = sm[i00], e01 = sm[i01], e10 = sm[i10], e11 = sm[i11];
-    Cx<P> a{P::re(e00), P::im(e00)}, bb{P::re(e01), P::im(e01)};
-    Cx<P> c{P::re(e10), P::im(e10)}, d{P::re(e11), P::im(e11)};
+  for (int b = threadIdx.x; b < nb; b += NT) {
+    const int c0 = ins0i(b & ((1 << ncb_log2) - 1), op.cbit[0]);
+    const int r0 = ins0i(b >> ncb_log2, op.rbit[0]);
+    const int i00 = gm.idx(r0, c0);
+    const int i01 = (i00 + ca) ^ cx, i10 = (i00 + ra) ^ rx;
+    const int i11 = (i10 + ca) ^ cx;
+    Cx<P> a = ld<P>(sm, i00), bb = ld<P>(sm, i01), c = ld<P>(sm, i10), d = ld<P>(sm, i11);
     if (op.kind == OP_PTM1_U) body_ptm1_u<P>(a, bb, c, d, cf);
     else if (op.kind == OP_PTM1_AD) body_ptm1_ad<P>(a, bb, c, d, cf);
     else body_ptm1<P>(a, bb, c, d, cf);
-    sm[i00] = P::make(a.re, a.im);
-    sm[i01] = P::make(bb.re, bb.im);
-    sm[i10] = P::make(c.re, c.im);
-    sm[i11] = P::make(d.re, d.im);
+    st<P>(sm, i00, a);
+    st<P>(sm, i01, bb);
+    st<P>(sm, i10, c);
+    st<P>(sm, i11, d);
   }
 }
 
-template <class P>
-__device__ __forceinline__ void apply_2q(typename P::Elem* sm, const SMap& mp, const PassOp& op,
-                                         const double* coef, int rows_log2g, int cols_log2g) {
+// Two-qubit unitary as two separable sweeps (V h V^dagger = V (h V^dagger)):
+// every row gets h[r, :] <- h[r, :] V^dagger on the column bits, then every
+// column gets h[:, c] <- V h[:, c] on the row bits.  Same 32 multiply-adds per
+// element as the block form, in 4-element units (small code, few registers).
+template <class P, int NT>
+__device__ __forceinline__ void apply_u2_sep(typename P::Elem* sm, const GMap<P>& gm, const PassOp& op,
+                                             const double* coef, int rows_log2g, int cols_log2g) {
+  const double* cf = coef + op.coef;
+  {
+    int a0, x0, a1, x1;
+    gm.col_delta(op.cbit[0], a0, x0);
+    gm.col_delta(op.cbit[1], a1, x1);
+    const int nc_log2 = cols_log2g - 2;
+    const int nu = 1 << (rows_log2g + nc_log2);
+    for (int u = threadIdx.x; u < nu; u += NT) {
+      const int li = u >> nc_log2;
+      const int c0 = ins0i(ins0i(u & ((1 << nc_log2) - 1), op.cbit[0]), op.cbit[1]);
+      int ix[4];
+      ix[0] = gm.idx(li, c0);
+      ix[1] = (ix[0] + a0) ^ x0;
+      ix[2] = (ix[0] + a1) ^ x1;
+      ix[3] = (ix[1] + a1) ^ x1;
+      Cx<P> in[4], out[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) in[a] = ld<P>(sm, ix[a]);
+      matvec4<P, true>(in, out, cf);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) st<P>(sm, ix[a], out[a]);
+    }
+  }
+  __syncthreads();
+  {
+    int a0, x0, a1, x1;
+    gm.row_delta(op.rbit[0], a0, x0);
+    gm.row_delta(op.rbit[1], a1, x1);
+    const int nu = 1 << (rows_log2g - 2 + cols_log2g);
+    for (int u = threadIdx.x; u < nu; u += NT) {
+      const int lj = u & ((1 << cols_log2g) - 1);
+      const int r0 = ins0i(ins0i(u >> cols_log2g, op.rbit[0]), op.rbit[1]);
+      int ix[4];
+      ix[0] = gm.idx(r0, lj);
+      ix[1] = (ix[0] + a0) ^ x0;
+      ix[2] = (ix[0] + a1) ^ x1;
+      ix[3] = (ix[1] + a1) ^ x1;
+      Cx<P> in[4], out[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) in[a] = ld<P>(sm, ix[a]);
+      matvec4<P, false>(in, out, cf);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) st<P>(sm, ix[a], out[a]);
+    }
+  }
+}
+
+template <class P, int NT>
+__device__ __noinline__ void apply_ptm2(typename P::Elem* sm, const GMap<P>& gm, const PassOp& op,
+                                           const double* coef, int rows_log2g, int cols_log2g) {
   const int ncb_log2 = cols_log2g - 2;
   const int nb = 1 << (rows_log2g - 2 + ncb_log2);
   const double* cf = coef + op.coef;
-  for (int b = threadIdx.x; b < nb; b += kThreads) {
-    const int cb = b & ((1 << ncb_log2) - 1);
-    const int rb = b >> ncb_log2;
-    const int c0 = ins0i(ins0i(cb, op.cbit[0]), op.cbit[1]);
-    const int r0 = ins0i(ins0i(rb, op.rbit[0]), op.rbit[1]);
-    int rows[4], cols[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      rows[a] = r0 | ((a & 1) << op.rbit[0]) | ((a >> 1) << op.rbit[1]);
-      cols[a] = c0 | ((a & 1) << op.cbit[0]) | ((a >> 1) << op.cbit[1]);
-    }
-    int idx[16];
+  int ra0, rx0, ra1, rx1, ca0, cx0, ca1, cx1;
+  gm.row_delta(op.rbit[0], ra0, rx0);
+  gm.row_delta(op.rbit[1], ra1, rx1);
+  gm.col_delta(op.cbit[0], ca0, cx0);
+  gm.col_delta(op.cbit[1], ca1, cx1);
+  for (int b = threadIdx.x; b < nb; b += NT) {
+    const int c0 = ins0i(ins0i(b & ((1 << ncb_log2) - 1), op.cbit[0]), op.cbit[1]);
+    const int r0 = ins0i(ins0i(b >> ncb_log2, op.rbit[0]), op.rbit[1]);
+    int rowi[4], ix[16];
+    rowi[0] = gm.idx(r0, c0);
+    rowi[1] = (rowi[0] + ra0) ^ rx0;
+    rowi[2] = (rowi[0] + ra1) ^ rx1;
+    rowi[3] = (rowi[1] + ra1) ^ rx1;
     Cx<P> h[16];
 #pragma unroll
-    for (int ra = 0; ra < 4; ++ra)
+    for (int r = 0; r < 4; ++r) {
+      ix[4 * r] = rowi[r];
+      ix[4 * r + 1] = (rowi[r] + ca0) ^ cx0;
+      ix[4 * r + 2] = (rowi[r] + ca1) ^ cx1;
+      ix[4 * r + 3] = (ix[4 * r + 1] + ca1) ^ cx1;
 #pragma unroll
-      for (int ca = 0; ca < 4; ++ca) {
-        idx[4 * ra + ca] = mp.idx(rows[ra], cols[ca]);
-        const auto e = sm[idx[4 * ra + ca]];
-        h[4 * ra + ca] = Cx<P>{P::re(e), P::im(e)};
-      }
-    if (op.kind == OP_U2) {
-      body_u2<P>(h, cf);
-#pragma unroll
-      for (int t = 0; t < 16; ++t) sm[idx[t]] = P::make(h[t].re, h[t].im);
-    } else {
-      body_ptm2<P>(h, cf);
-#pragma unroll
-      for (int t = 0; t < 16; ++t) sm[idx[t]] = P::make(h[t].re, h[t].im);
+      for (int c = 0; c < 4; ++c) h[4 * r + c] = ld<P>(sm, ix[4 * r + c]);
     }
+    body_ptm2<P>(h, cf);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) st<P>(sm, ix[t], h[t]);
   }
 }
+
+// ------------------------------------------------------------------ async copies (Ampere-style LDGSTS)
+__device__ __forceinline__ void cp_async16(void* smem_ptr, const void* gmem_ptr) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_ptr));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_ptr) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_ptr, const void* gmem_ptr) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_ptr));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_ptr) : "memory");
+}
+template <class E>
+__device__ __forceinline__ void cp_async_elem(E* smem_ptr, const E* gmem_ptr) {
+  if constexpr (sizeof(E) == 16) cp_async16(smem_ptr, gmem_ptr);
+  else cp_async8(smem_ptr, gmem_ptr);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------ the pass kernel
+// Persistent CTAs walk the work items with a two-stage shared-memory
+// pipeline: the 16-byte asynchronous copies of item i + 1 are in flight while
+// item i is transformed and written back, so HBM reads overlap the arithmetic.
+constexpr int kMainThreads = 512;
+
 template <class P, int H>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kMainThreads, 1)
 pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc d) {
   using E = typename P::Elem;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  E* sm = reinterpret_cast<E*>(smem_raw);
   constexpr int S = 1 << H;
-  const int m = d.m;
-  const int M = 1 << m;
-  const int rl = d.rows_log2;
-  const int R = 1 << rl;
+  constexpr int NSLOT = S * S;
+  constexpr int GPE = 16 / int(sizeof(E));   // elements per 16-byte granule
+  constexpr int GSH = GPE == 2 ? 1 : 0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int64_t s_base[2][NSLOT];
+  __shared__ unsigned s_tmask[2];
+  __shared__ int s_diag[2];
+  E* bufs = reinterpret_cast<E*>(smem_raw);
+  const int m = d.m, M = 1 << m;
+  const int rl = d.rows_log2, R = 1 << rl;
   const int slot_log2 = rl + m;
-  const int total = (S * S) << slot_log2;
+  const int buf_elems = NSLOT << slot_log2;
+  const int sw = min(7, (M >> GSH) - 1);
+  const int64_t chunk_mask = (int64_t(1) << d.chunks_log2) - 1;
   const int64_t tile_elems = int64_t(1) << (2 * m);
-  SMap mp{rl, m, H, P::kSwizzle & (M - 1)};
   const int rows_log2g = H + rl, cols_log2g = H + m;
+  const GMap<P> gm{rl, m, H, sw};
 
-  for (int64_t w = blockIdx.x; w < d.n_items; w += gridDim.x) {
-    const int64_t g = w >> d.chunks_log2;
-    const int r0 = int(w & ((int64_t(1) << d.chunks_log2) - 1)) << rl;
-    // chunked passes leave the diagonal groups to pass_kernel_diag and walk
-    // the strictly lower groups only (g = tic (tic - 1) / 2 + tjc, tjc < tic)
-    const int64_t tic = d.skip_diag ? tri_row(g) + 1 : tri_row(g);
-    const int64_t tjc = d.skip_diag ? g - tic * (tic - 1) / 2 : g - tic * (tic + 1) / 2;
-    int64_t bi = tic, bj = tjc;
+  // slot bases, the transposed mask and the diagonal flag of item w -> stage b (warp 0)
+  auto item_info = [&](int64_t w, int b) {
+    if (threadIdx.x < 32) {
+      const int64_t g = w >> d.chunks_log2;
+      const int64_t tic = d.skip_diag ? tri_row(g) + 1 : tri_row(g);
+      const int64_t tjc = d.skip_diag ? g - tic * (tic - 1) / 2 : g - tic * (tic + 1) / 2;
+      bool t = false;
+      if (int(threadIdx.x) < NSLOT) {
+        int64_t ti = tic, tj = tjc;
 #pragma unroll
-    for (int l = 0; l < H; ++l) { bi = ins0(bi, d.hpos[l]); bj = ins0(bj, d.hpos[l]); }
-    const bool diag_group = (tic == tjc);
-
-    // ---- load: global -> shared, upper slots transposed + conjugated
-#pragma unroll 4
-    for (int e = threadIdx.x; e < total; e += kThreads) {
-      const int slot = e >> slot_log2;
-      const int within = e & ((1 << slot_log2) - 1);
-      const int x = slot >> H, y = slot & (S - 1);
-      int64_t ti = bi, tj = bj;
+        for (int l = 0; l < H; ++l) { ti = ins0(ti, d.hpos[l]); tj = ins0(tj, d.hpos[l]); }
+        const int x = int(threadIdx.x) >> H, y = int(threadIdx.x) & (S - 1);
 #pragma unroll
-      for (int l = 0; l < H; ++l) {
-        ti |= int64_t((x >> l) & 1) << d.hpos[l];
-        tj |= int64_t((y >> l) & 1) << d.hpos[l];
+        for (int l = 0; l < H; ++l) {
+          ti |= int64_t((x >> l) & 1) << d.hpos[l];
+          tj |= int64_t((y >> l) & 1) << d.hpos[l];
+        }
+        t = ti < tj;
+        s_base[b][threadIdx.x] = (t ? tj * (tj + 1) / 2 + ti : ti * (ti + 1) / 2 + tj) * tile_elems;
       }
-      if (ti >= tj) {
-        const int r = within >> m, c = within & (M - 1);
-        const int64_t off = (ti * (ti + 1) / 2 + tj) * tile_elems + int64_t(r0 + r) * M + c;
-        sm[(slot << slot_log2) + (r << m) + (c ^ (r & mp.sw))] = st[off];
-      } else {
-        const int r = within & (R - 1), c = within >> rl;
-        const int64_t off = (tj * (tj + 1) / 2 + ti) * tile_elems + int64_t(c) * M + (r0 + r);
-        sm[(slot << slot_log2) + (r << m) + (c ^ (r & mp.sw))] = P::conj(st[off]);
+      const unsigned mask = __ballot_sync(0xffffffffu, t);
+      if (threadIdx.x == 0) {
+        s_tmask[b] = mask;
+        s_diag[b] = (tic == tjc);
       }
     }
+  };
+  // Asynchronous loads of item w into stage b: rows of lower slots as
+  // 16-byte granules; upper slots element by element into their transposed
+  // (logical) place, reading the stored partner along its rows.
+  auto issue_loads = [&](int64_t w, int b) {
+    E* buf = bufs + b * buf_elems;
+    const int r0 = int(w & chunk_mask) << rl;
+    const unsigned tm = s_tmask[b];
+#pragma unroll 1
+    for (int slot = 0; slot < NSLOT; ++slot) {
+      const int64_t base = s_base[b][slot];
+      E* sbuf = buf + (slot << slot_log2);
+      if (!((tm >> slot) & 1u)) {
+        for (int g = threadIdx.x; g < (1 << (slot_log2 - GSH)); g += kMainThreads) {
+          const int within = g << GSH;
+          const int pr = within >> m, pc = within & (M - 1);
+          cp_async16(sbuf + (pr << m) + (pc ^ ((pr & sw) << GSH)), st + base + int64_t(r0 + pr) * M + pc);
+        }
+      } else {
+        for (int e = threadIdx.x; e < (1 << slot_log2); e += kMainThreads) {
+          const int sr = e >> rl, sc = e & (R - 1);   // stored row / column (within the chunk)
+          cp_async_elem(sbuf + (sc << m) + (sr ^ ((sc & sw) << GSH)), st + base + int64_t(sr) * M + r0 + sc);
+        }
+      }
+    }
+  };
+
+  int64_t w = blockIdx.x;
+  if (w < d.n_items) item_info(w, 0);
+  __syncthreads();
+  if (w < d.n_items) issue_loads(w, 0);
+  cp_async_commit();
+  for (int it = 0; w < d.n_items; ++it, w += gridDim.x) {
+    const int cur = it & 1, nxt = cur ^ 1;
+    const int64_t wn = w + gridDim.x;
+    if (wn < d.n_items) item_info(wn, nxt);
+    __syncthreads();
+    if (wn < d.n_items) issue_loads(wn, nxt);
+    cp_async_commit();
+    cp_async_wait_prev();
     __syncthreads();
 
-    // ---- the fused ops
-    for (int o = 0; o < d.nops; ++o) {
-      const PassOp& op = d.ops[o];
-      if (op.nq == 1) apply_1q<P>(sm, mp, op, d.coef, rows_log2g, cols_log2g);
-      else apply_2q<P>(sm, mp, op, d.coef, rows_log2g, cols_log2g);
+    E* sm = bufs + cur * buf_elems;
+    const unsigned tm = s_tmask[cur];
+    if (tm) {   // upper slots arrive transposed but not yet conjugated
+#pragma unroll 1
+      for (int slot = 0; slot < NSLOT; ++slot) {
+        if (!((tm >> slot) & 1u)) continue;
+        E* sbuf = sm + (slot << slot_log2);
+        for (int e = threadIdx.x; e < (1 << slot_log2); e += kMainThreads) sbuf[e] = P::conj_if(sbuf[e], 1u);
+      }
       __syncthreads();
     }
-
-    // ---- store: shared -> global, each stored tile exactly once
-#pragma unroll 4
-    for (int e = threadIdx.x; e < total; e += kThreads) {
-      const int slot = e >> slot_log2;
-      const int within = e & ((1 << slot_log2) - 1);
-      const int x = slot >> H, y = slot & (S - 1);
-      int64_t ti = bi, tj = bj;
-#pragma unroll
-      for (int l = 0; l < H; ++l) {
-        ti |= int64_t((x >> l) & 1) << d.hpos[l];
-        tj |= int64_t((y >> l) & 1) << d.hpos[l];
-      }
-      if (ti >= tj) {
-        const int r = within >> m, c = within & (M - 1);
-        const int64_t off = (ti * (ti + 1) / 2 + tj) * tile_elems + int64_t(r0 + r) * M + c;
-        st[off] = sm[(slot << slot_log2) + (r << m) + (c ^ (r & mp.sw))];
-      } else if (!diag_group) {
-        const int r = within & (R - 1), c = within >> rl;
-        const int64_t off = (tj * (tj + 1) / 2 + ti) * tile_elems + int64_t(c) * M + (r0 + r);
-        st[off] = P::conj(sm[(slot << slot_log2) + (r << m) + (c ^ (r & mp.sw))]);
+    for (int o = 0; o < d.nops; ++o) {
+      const PassOp& op = d.ops[o];
+      if (op.nq == 1) apply_1q<P, kMainThreads>(sm, gm, op, d.coef, rows_log2g, cols_log2g);
+      else if (op.kind == OP_U2) apply_u2_sep<P, kMainThreads>(sm, gm, op, d.coef, rows_log2g, cols_log2g);
+      else apply_ptm2<P, kMainThreads>(sm, gm, op, d.coef, rows_log2g, cols_log2g);
+      __syncthreads();
+    }
+    // write back, each stored tile exactly once: lower slots as 16-byte row
+    // granules, upper slots conjugated into their stored partner (skipped in
+    // a diagonal group, where they mirror lower slots of the same group)
+    const int r0 = int(w & chunk_mask) << rl;
+#pragma unroll 1
+    for (int slot = 0; slot < NSLOT; ++slot) {
+      const int64_t base = s_base[cur][slot];
+      const E* sbuf = sm + (slot << slot_log2);
+      if (!((tm >> slot) & 1u)) {
+        for (int g = threadIdx.x; g < (1 << (slot_log2 - GSH)); g += kMainThreads) {
+          const int within = g << GSH;
+          const int pr = within >> m, pc = within & (M - 1);
+          *reinterpret_cast<uint4*>(st + base + int64_t(r0 + pr) * M + pc) =
+              *reinterpret_cast<const uint4*>(sbuf + (pr << m) + (pc ^ ((pr & sw) << GSH)));
+        }
+      } else if (!s_diag[cur]) {
+        for (int e = threadIdx.x; e < (1 << slot_log2); e += kMainThreads) {
+          const int sr = e >> rl, sc = e & (R - 1);
+          st[base + int64_t(sr) * M + r0 + sc] = P::conj_if(sbuf[(sc << m) + (sr ^ ((sc & sw) << GSH))], 1u);
+        }
       }
     }
     __syncthreads();
   }
 }
-
 
 // ------------------------------------------------------------------ diagonal groups
 // A diagonal group (ti == tj before the high bits are inserted) is hermitian
@@ -542,8 +716,8 @@ struct LaunchCache {
 };
 
 template <class E>
-cudaError_t launch_one(void (*kfn)(E*, PassDesc), LaunchCache& lc, size_t smem, int64_t items, void* state,
-                       const PassDesc& d, cudaStream_t s) {
+cudaError_t launch_one(void (*kfn)(E*, PassDesc), LaunchCache& lc, int threads, size_t smem, int64_t items,
+                       void* state, const PassDesc& d, cudaStream_t s) {
   if (items <= 0) return cudaSuccess;
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
@@ -552,7 +726,7 @@ cudaError_t launch_one(void (*kfn)(E*, PassDesc), LaunchCache& lc, size_t smem, 
     err = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (err != cudaSuccess) return err;
     int nb = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, kThreads, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, threads, smem);
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&lc.sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
@@ -562,23 +736,30 @@ cudaError_t launch_one(void (*kfn)(E*, PassDesc), LaunchCache& lc, size_t smem, 
   }
   int64_t grid = int64_t(lc.blocks) * lc.sms;
   if (grid > items) grid = items;
-  kfn<<<dim3(unsigned(grid)), dim3(kThreads), smem, s>>>(reinterpret_cast<E*>(state), d);
+  kfn<<<dim3(unsigned(grid)), dim3(threads), smem, s>>>(reinterpret_cast<E*>(state), d);
   return cudaGetLastError();
 }
 
 template <class P, int H>
 cudaError_t launch_t(void* state, const PassDesc& d, cudaStream_t s, int* launches) {
   using E = typename P::Elem;
+  constexpr int S_DIAG = (1 << H) * ((1 << H) + 1) / 2;   // stored slots of a diagonal group
   static thread_local LaunchCache main_cache, diag_cache;
-  const size_t smem = sizeof(E) * (size_t(1) << (2 * H + d.rows_log2 + d.m));
-  cudaError_t err = launch_one<E>(pass_kernel<P, H>, main_cache, smem, d.n_items, state, d, s);
+  // two pipeline stages of one tile group each
+  const size_t smem = 2 * sizeof(E) * (size_t(1) << (2 * H + d.rows_log2 + d.m));
+  cudaError_t err = launch_one<E>(pass_kernel<P, H>, main_cache, kMainThreads, smem, d.n_items, state, d, s);
   if (err != cudaSuccess) return err;
   int n = d.n_items > 0 ? 1 : 0;
-  if (d.skip_diag) {
-    const size_t dsmem = sizeof(E) * size_t((1 << H) * ((1 << H) + 1) / 2) * (size_t(1) << (2 * d.m));
-    err = launch_one<E>(pass_kernel_diag<P, H>, diag_cache, dsmem, d.nt_c, state, d, s);
-    if (err != cudaSuccess) return err;
-    n += 1;
+  // only two-high-qubit passes are row-chunked (tile_log2 <= 5)
+  if constexpr (H == 2) {
+    if (d.skip_diag) {
+      const size_t dsmem = sizeof(E) * size_t(S_DIAG) * (size_t(1) << (2 * d.m));
+      err = launch_one<E>(pass_kernel_diag<P, H>, diag_cache, kThreads, dsmem, d.nt_c, state, d, s);
+      if (err != cudaSuccess) return err;
+      n += 1;
+    }
+  } else {
+    if (d.skip_diag) return cudaErrorInvalidValue;
   }
   if (launches) *launches = n;
   return cudaSuccess;
