@@ -167,7 +167,7 @@ def traffic_record(dtype: str):
     """DRAM bytes per pass-kernel launch from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "pass_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_2604_15765_gb300", "csrc", "pass_kernels.cu")
+    src = os.path.join(ROOT, "paper_2604_15765_gb300", "csrc", "pass_kernels.cuh")
     try:
         with open(path) as f:
             rec = json.load(f)

@@ -113,7 +113,7 @@ int orkan_ptm(int k, int r, const double *K, int adjoint, double *out);
 /* ------------------------------------------------------------------ lifetime */
 
 /* Allocate an n-qubit operator (1 <= n <= 24) with tile edge 2^tile_log2
- * (2 <= tile_log2 <= 5; the paper's m = 5 is the default when tile_log2 is 0)
+ * (3 <= tile_log2 <= 5; the paper's m = 5 is the default when tile_log2 is 0)
  * on the current CUDA device.  The content is undefined until an init call.
  * Errors: EINVAL, ENOMEM, ENODEV, ECUDA. */
 int orkan_alloc(int n, int dtype, int tile_log2, orkan_h *out);

@@ -148,7 +148,7 @@ extern "C" int orkan_expect_paulis_noalloc(const void* dev_state, int n, int dty
   using namespace orkan;
   if (tile_log2 == 0) tile_log2 = 5;
   if (!dev_state || !paulis || !out) return na_fail(ORKAN_EINVAL, "null argument");
-  if (n < 1 || n > 24 || tile_log2 < 2 || tile_log2 > 5 || (dtype != DT_C128 && dtype != DT_C64 && dtype != DT_DF64))
+  if (n < 1 || n > 24 || tile_log2 < 3 || tile_log2 > 5 || (dtype != DT_C128 && dtype != DT_C64 && dtype != DT_DF64))
     return na_fail(ORKAN_EINVAL, "bad n / dtype / tile_log2");
   if (count < 1 || count > kNaMax)
     return na_fail(ORKAN_EINVAL, "count must be between 1 and ORKAN_NOALLOC_MAX_STRINGS (" +

@@ -266,7 +266,9 @@ void pack_coef(const orkan_ctx* h, PassDesc& d, int slot, double v) {
 int flush_pending(orkan_ctx* h) {
   if (h->pending.empty()) return ORKAN_OK;
   const PassShape s = shape_of(h, h->pending, nullptr);
-  const int rl = rows_log2_for(h, s.nh);
+  // in-tile passes run with four independent tiles per work item, on the
+  // one-high-qubit group geometry
+  const int rl = rows_log2_for(h, s.nh == 0 ? 1 : s.nh);
   PassDesc d;
   std::memset(&d, 0, sizeof(d));
   d.m = h->g.m;
@@ -281,6 +283,8 @@ int flush_pending(orkan_ctx* h) {
   d.skip_diag = d.chunks_log2 > 0 ? 1 : 0;
   const int64_t groups = d.skip_diag ? d.nt_c * (d.nt_c - 1) / 2 : d.nt_c * (d.nt_c + 1) / 2;
   d.n_items = groups << d.chunks_log2;
+  d.n_tiles = h->g.ntiles;
+  if (s.nh == 0) d.n_items = (h->g.ntiles + 3) / 4;
   int slot = 0;
   for (const HostOp& op : h->pending) {
     PassOp& po = d.ops[d.nops++];
@@ -298,6 +302,7 @@ int flush_pending(orkan_ctx* h) {
       }
     }
     po.coef = slot;
+    if (op.kind == OP_PTM2) d.has_ptm2 = 1;
     const std::vector<double> c = op.nq == 1 ? coef_1q(op.kind, op.R) : op.coef;
     for (double v : c) pack_coef(h, d, slot++, v);
   }
@@ -459,7 +464,7 @@ void release_handle(orkan_ctx* c) {
 
 bool geometry(int n, int tile_log2, Geometry* g) {
   if (tile_log2 == 0) tile_log2 = 5;
-  if (n < 1 || n > 24 || tile_log2 < 2 || tile_log2 > 5) return false;
+  if (n < 1 || n > 24 || tile_log2 < 3 || tile_log2 > 5) return false;
   g->n = n;
   g->m = tile_log2;
   g->N = int64_t(1) << n;

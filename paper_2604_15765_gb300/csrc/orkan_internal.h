@@ -51,7 +51,10 @@ struct PassOp {
 // h high-qubit bits into a base tile pair (ti, tj) of the compressed grid, as
 // in Algorithm 3 -- restricted to a chunk of 2^rows_log2 rows of each tile.
 struct PassDesc {
-  int64_t n_items;     // groups * chunks
+  int64_t n_items;     // work items: groups * chunks, or ceil(n_tiles / 4) for in-tile passes
+  int64_t n_tiles;     // stored tiles
+  int32_t has_ptm2;    // 1 if an op of the pass is a generic two-qubit map
+  int32_t pad0;
   int64_t nt_c;        // edge of the compressed tile grid (Nt >> h)
   int32_t m;           // tile_log2
   int32_t h;           // number of high (cross-tile) qubits, 0..2

@@ -21,6 +21,7 @@
 // Shared memory holds each slot row-major with the 16-byte (8-byte) element
 // index XOR-swizzled by the row, so that transposed loads/stores and
 // strided butterfly accesses hit distinct banks.
+#pragma once
 #include "orkan_internal.h"
 #include "numeric.cuh"
 #include "device_util.cuh"
@@ -46,23 +47,26 @@ __device__ __forceinline__ int ins0i(int x, int p) {
 //   idx = ((x 2^H + y) R + r) M + (c ^ ((r & sw) << SH)).
 // Slots whose tile lies in the upper triangle are loaded already transposed
 // and conjugated, so every op sees plain logical elements.
-template <class P>
+template <class P, int H, int MLOG, int RL>
 struct GMap {
-  int rl, m, H, sw;
-  __device__ __forceinline__ int idx(int li, int lj) const {
-    const int x = li >> rl, r = li & ((1 << rl) - 1);
-    const int y = lj >> m, c = lj & ((1 << m) - 1);
-    return ((((x << H) | y) << rl | r) << m) + (c ^ ((r & sw) << P::kSwShift));
+  static constexpr int M = 1 << MLOG;
+  static constexpr int R = 1 << RL;
+  static constexpr int SH = P::kSwShift;
+  static constexpr int SW = ((M >> SH) - 1) < 7 ? ((M >> SH) - 1) : 7;
+  static __device__ __forceinline__ int idx(int li, int lj) {
+    const int x = li >> RL, r = li & (R - 1);
+    const int y = lj >> MLOG, c = lj & (M - 1);
+    return ((((x << H) | y) << RL | r) << MLOG) + (c ^ ((r & SW) << SH));
   }
   // index of the partner whose row (or column) index has bit `pos` set, as
   // idx' = (idx + add) ^ xr, for an element whose index has that bit clear
-  __device__ __forceinline__ void row_delta(int pos, int& add, int& xr) const {
-    if (pos < rl) { add = (1 << pos) << m; xr = ((1 << pos) & sw) << P::kSwShift; }
-    else { add = (1 << (pos - rl)) << (H + rl + m); xr = 0; }
+  static __device__ __forceinline__ void row_delta(int pos, int& add, int& xr) {
+    if (pos < RL) { add = (1 << pos) << MLOG; xr = ((1 << pos) & SW) << SH; }
+    else { add = (1 << (pos - RL)) << (H + RL + MLOG); xr = 0; }
   }
-  __device__ __forceinline__ void col_delta(int pos, int& add, int& xr) const {
-    if (pos < m) { add = 0; xr = 1 << pos; }
-    else { add = (1 << (pos - m)) << (rl + m); xr = 0; }
+  static __device__ __forceinline__ void col_delta(int pos, int& add, int& xr) {
+    if (pos < MLOG) { add = 0; xr = 1 << pos; }
+    else { add = (1 << (pos - MLOG)) << (RL + MLOG); xr = 0; }
   }
 };
 
@@ -303,15 +307,15 @@ __device__ __forceinline__ void matvec4(const Cx<P> (&in)[4], Cx<P> (&out)[4], c
 }
 
 // ------------------------------------------------------------------ op drivers
-template <class P, int NT>
-__device__ __forceinline__ void apply_1q(typename P::Elem* sm, const GMap<P>& gm, const PassOp& op,
-                                         const double* coef, int rows_log2g, int cols_log2g) {
-  const int ncb_log2 = cols_log2g - 1;
-  const int nb = 1 << (rows_log2g - 1 + ncb_log2);
+template <class P, class G, int NT, int rows_log2g, int cols_log2g>
+__device__ __forceinline__ void apply_1q(typename P::Elem* sm, const G& gm, const PassOp& op, const double* coef) {
+  constexpr int ncb_log2 = cols_log2g - 1;
+  constexpr int nb = 1 << (rows_log2g - 1 + ncb_log2);
   int ra, rx, ca, cx;
   gm.row_delta(op.rbit[0], ra, rx);
   gm.col_delta(op.cbit[0], ca, cx);
   const double* cf = coef + op.coef;
+#pragma unroll(P::kOpUnroll)
   for (int b = threadIdx.x; b < nb; b += NT) {
     const int c0 = ins0i(b & ((1 << ncb_log2) - 1), op.cbit[0]);
     const int r0 = ins0i(b >> ncb_log2, op.rbit[0]);
@@ -333,16 +337,17 @@ __device__ __forceinline__ void apply_1q(typename P::Elem* sm, const GMap<P>& gm
 // every row gets h[r, :] <- h[r, :] V^dagger on the column bits, then every
 // column gets h[:, c] <- V h[:, c] on the row bits.  Same 32 multiply-adds per
 // element as the block form, in 4-element units (small code, few registers).
-template <class P, int NT>
-__device__ __forceinline__ void apply_u2_sep(typename P::Elem* sm, const GMap<P>& gm, const PassOp& op,
-                                             const double* coef, int rows_log2g, int cols_log2g) {
+template <class P, class G, int NT, int rows_log2g, int cols_log2g>
+__device__ __forceinline__ void apply_u2_sep(typename P::Elem* sm, const G& gm, const PassOp& op,
+                                             const double* coef) {
   const double* cf = coef + op.coef;
   {
     int a0, x0, a1, x1;
     gm.col_delta(op.cbit[0], a0, x0);
     gm.col_delta(op.cbit[1], a1, x1);
-    const int nc_log2 = cols_log2g - 2;
-    const int nu = 1 << (rows_log2g + nc_log2);
+    constexpr int nc_log2 = cols_log2g - 2;
+    constexpr int nu = 1 << (rows_log2g + nc_log2);
+#pragma unroll(P::kOpUnroll)
     for (int u = threadIdx.x; u < nu; u += NT) {
       const int li = u >> nc_log2;
       const int c0 = ins0i(ins0i(u & ((1 << nc_log2) - 1), op.cbit[0]), op.cbit[1]);
@@ -364,7 +369,8 @@ __device__ __forceinline__ void apply_u2_sep(typename P::Elem* sm, const GMap<P>
     int a0, x0, a1, x1;
     gm.row_delta(op.rbit[0], a0, x0);
     gm.row_delta(op.rbit[1], a1, x1);
-    const int nu = 1 << (rows_log2g - 2 + cols_log2g);
+    constexpr int nu = 1 << (rows_log2g - 2 + cols_log2g);
+#pragma unroll(P::kOpUnroll)
     for (int u = threadIdx.x; u < nu; u += NT) {
       const int lj = u & ((1 << cols_log2g) - 1);
       const int r0 = ins0i(ins0i(u >> cols_log2g, op.rbit[0]), op.rbit[1]);
@@ -383,9 +389,8 @@ __device__ __forceinline__ void apply_u2_sep(typename P::Elem* sm, const GMap<P>
   }
 }
 
-template <class P, int NT>
-__device__ __noinline__ void apply_ptm2(typename P::Elem* sm, const GMap<P>& gm, const PassOp& op,
-                                           const double* coef, int rows_log2g, int cols_log2g) {
+template <class P, class G, int NT, int rows_log2g, int cols_log2g>
+__device__ __forceinline__ void apply_ptm2(typename P::Elem* sm, const G& gm, const PassOp& op, const double* coef) {
   const int ncb_log2 = cols_log2g - 2;
   const int nb = 1 << (rows_log2g - 2 + ncb_log2);
   const double* cf = coef + op.coef;
@@ -418,6 +423,15 @@ __device__ __noinline__ void apply_ptm2(typename P::Elem* sm, const GMap<P>& gm,
   }
 }
 
+// Rows of each tile held per work item: the largest 2^RL <= M with
+// 4^H tiles x 2^RL rows x M elements within 64 KiB of shared memory per stage
+// (the host planner makes the same choice; the launcher checks it).
+__host__ __device__ constexpr int rows_log2_ct(int H, int MLOG, int eb) {
+  int rl = 0;
+  while (rl < MLOG && ((long long)(1 << (2 * H)) * (1 << MLOG) * eb << (rl + 1)) <= 64 * 1024) ++rl;
+  return rl;
+}
+
 // ------------------------------------------------------------------ async copies (Ampere-style LDGSTS)
 __device__ __forceinline__ void cp_async16(void* smem_ptr, const void* gmem_ptr) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_ptr));
@@ -434,6 +448,7 @@ __device__ __forceinline__ void cp_async_elem(E* smem_ptr, const E* gmem_ptr) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------ the pass kernel
 // Persistent CTAs walk the work items with a two-stage shared-memory
@@ -441,7 +456,11 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 // item i is transformed and written back, so HBM reads overlap the arithmetic.
 constexpr int kMainThreads = 512;
 
-template <class P, int H>
+// PACK: an in-tile pass (no high qubit) runs on the H = 1 geometry with four
+// consecutive stored tiles as the four independent slots of a work item.
+// P2: the pass contains a generic two-qubit map (PTM2); its large body is
+// compiled only into these instantiations.
+template <class P, int H, int MLOG, bool PACK, bool P2>
 __global__ void __launch_bounds__(kMainThreads, 1)
 pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc d) {
   using E = typename P::Elem;
@@ -449,131 +468,176 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
   constexpr int NSLOT = S * S;
   constexpr int GPE = 16 / int(sizeof(E));   // elements per 16-byte granule
   constexpr int GSH = GPE == 2 ? 1 : 0;
+  constexpr int RL = rows_log2_ct(H, MLOG, int(sizeof(E)));
+  using G = GMap<P, H, MLOG, RL>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int64_t s_base[2][NSLOT];
-  __shared__ unsigned s_tmask[2];
-  __shared__ int s_diag[2];
+  // per-item slot info, three items deep: item i+2 is decoded while item i+1
+  // loads and item i computes
+  __shared__ int64_t s_base[3][NSLOT];
+  __shared__ unsigned s_tmask[3], s_vmask[3];
+  __shared__ int s_diag[3];
   E* bufs = reinterpret_cast<E*>(smem_raw);
-  const int m = d.m, M = 1 << m;
-  const int rl = d.rows_log2, R = 1 << rl;
-  const int slot_log2 = rl + m;
-  const int buf_elems = NSLOT << slot_log2;
-  const int sw = min(7, (M >> GSH) - 1);
+  constexpr int m = MLOG, M = 1 << MLOG;
+  constexpr int rl = RL, R = 1 << RL;
+  constexpr int slot_log2 = rl + m;
+  constexpr int buf_elems = NSLOT << slot_log2;
+  constexpr int sw = G::SW;
+  constexpr int rows_log2g = H + rl, cols_log2g = H + m;
   const int64_t chunk_mask = (int64_t(1) << d.chunks_log2) - 1;
   const int64_t tile_elems = int64_t(1) << (2 * m);
-  const int rows_log2g = H + rl, cols_log2g = H + m;
-  const GMap<P> gm{rl, m, H, sw};
+  const G gm{};
 
-  // slot bases, the transposed mask and the diagonal flag of item w -> stage b (warp 0)
+  // slot bases, transposed / valid masks and the diagonal flag of item w (warp 0)
   auto item_info = [&](int64_t w, int b) {
     if (threadIdx.x < 32) {
-      const int64_t g = w >> d.chunks_log2;
-      const int64_t tic = d.skip_diag ? tri_row(g) + 1 : tri_row(g);
-      const int64_t tjc = d.skip_diag ? g - tic * (tic - 1) / 2 : g - tic * (tic + 1) / 2;
-      bool t = false;
-      if (int(threadIdx.x) < NSLOT) {
-        int64_t ti = tic, tj = tjc;
+      bool t = false, v = false;
+      int64_t tic = 0, tjc = 0;
+      if constexpr (PACK) {
+        const int64_t tile = w * NSLOT + threadIdx.x;
+        v = int(threadIdx.x) < NSLOT && tile < d.n_tiles;
+        if (v) s_base[b][threadIdx.x] = tile * tile_elems;
+      } else {
+        const int64_t g = w >> d.chunks_log2;
+        tic = d.skip_diag ? tri_row(g) + 1 : tri_row(g);
+        tjc = d.skip_diag ? g - tic * (tic - 1) / 2 : g - tic * (tic + 1) / 2;
+        if (int(threadIdx.x) < NSLOT) {
+          int64_t ti = tic, tj = tjc;
 #pragma unroll
-        for (int l = 0; l < H; ++l) { ti = ins0(ti, d.hpos[l]); tj = ins0(tj, d.hpos[l]); }
-        const int x = int(threadIdx.x) >> H, y = int(threadIdx.x) & (S - 1);
+          for (int l = 0; l < H; ++l) { ti = ins0(ti, d.hpos[l]); tj = ins0(tj, d.hpos[l]); }
+          const int x = int(threadIdx.x) >> H, y = int(threadIdx.x) & (S - 1);
 #pragma unroll
-        for (int l = 0; l < H; ++l) {
-          ti |= int64_t((x >> l) & 1) << d.hpos[l];
-          tj |= int64_t((y >> l) & 1) << d.hpos[l];
+          for (int l = 0; l < H; ++l) {
+            ti |= int64_t((x >> l) & 1) << d.hpos[l];
+            tj |= int64_t((y >> l) & 1) << d.hpos[l];
+          }
+          t = ti < tj;
+          v = true;
+          s_base[b][threadIdx.x] = (t ? tj * (tj + 1) / 2 + ti : ti * (ti + 1) / 2 + tj) * tile_elems;
         }
-        t = ti < tj;
-        s_base[b][threadIdx.x] = (t ? tj * (tj + 1) / 2 + ti : ti * (ti + 1) / 2 + tj) * tile_elems;
       }
-      const unsigned mask = __ballot_sync(0xffffffffu, t);
+      const unsigned tmask = __ballot_sync(0xffffffffu, t);
+      const unsigned vmask = __ballot_sync(0xffffffffu, v);
       if (threadIdx.x == 0) {
-        s_tmask[b] = mask;
-        s_diag[b] = (tic == tjc);
+        s_tmask[b] = tmask;
+        s_vmask[b] = vmask;
+        s_diag[b] = !PACK && (tic == tjc);
       }
     }
   };
-  // Asynchronous loads of item w into stage b: rows of lower slots as
+  // Asynchronous loads of item w into stage buffer `buf`: rows of lower slots as
   // 16-byte granules; upper slots element by element into their transposed
   // (logical) place, reading the stored partner along its rows.
-  auto issue_loads = [&](int64_t w, int b) {
-    E* buf = bufs + b * buf_elems;
+  auto issue_loads = [&](int64_t w, int b, E* buf) {
     const int r0 = int(w & chunk_mask) << rl;
-    const unsigned tm = s_tmask[b];
+    const unsigned tm = s_tmask[b], vm = s_vmask[b];
 #pragma unroll 1
     for (int slot = 0; slot < NSLOT; ++slot) {
-      const int64_t base = s_base[b][slot];
+      if (!((vm >> slot) & 1u)) continue;
+      const E* gbase = st + s_base[b][slot];
       E* sbuf = buf + (slot << slot_log2);
       if (!((tm >> slot) & 1u)) {
-        for (int g = threadIdx.x; g < (1 << (slot_log2 - GSH)); g += kMainThreads) {
-          const int within = g << GSH;
-          const int pr = within >> m, pc = within & (M - 1);
-          cp_async16(sbuf + (pr << m) + (pc ^ ((pr & sw) << GSH)), st + base + int64_t(r0 + pr) * M + pc);
+        constexpr int NG = 1 << (slot_log2 - GSH);
+#pragma unroll
+        for (int k = 0; k < (NG + kMainThreads - 1) / kMainThreads; ++k) {
+          const int g = int(threadIdx.x) + k * kMainThreads;
+          if (NG % kMainThreads == 0 || g < NG) {
+            const int within = g << GSH;
+            const int pr = within >> m, pc = within & (M - 1);
+            cp_async16(sbuf + (pr << m) + (pc ^ ((pr & sw) << GSH)), gbase + (r0 + pr) * M + pc);
+          }
         }
       } else {
-        for (int e = threadIdx.x; e < (1 << slot_log2); e += kMainThreads) {
-          const int sr = e >> rl, sc = e & (R - 1);   // stored row / column (within the chunk)
-          cp_async_elem(sbuf + (sc << m) + (sr ^ ((sc & sw) << GSH)), st + base + int64_t(sr) * M + r0 + sc);
+        constexpr int NE = 1 << slot_log2;
+#pragma unroll
+        for (int k = 0; k < (NE + kMainThreads - 1) / kMainThreads; ++k) {
+          const int e = int(threadIdx.x) + k * kMainThreads;
+          if (NE % kMainThreads == 0 || e < NE) {
+            const int sr = e >> rl, sc = e & (R - 1);   // stored row / column (within the chunk)
+            cp_async_elem(sbuf + (sc << m) + (sr ^ ((sc & sw) << GSH)), gbase + sr * M + r0 + sc);
+          }
         }
       }
     }
   };
 
+  // Three stages: item i computes in buffer i % 3 while the copies of item
+  // i + 1 fill buffer (i + 1) % 3; the slot info of item i + 2 is decoded
+  // meanwhile and made visible to all threads by the op barriers.
+  const int64_t G0 = gridDim.x;
   int64_t w = blockIdx.x;
   if (w < d.n_items) item_info(w, 0);
+  if (w + G0 < d.n_items) item_info(w + G0, 1);
   __syncthreads();
-  if (w < d.n_items) issue_loads(w, 0);
+  if (w < d.n_items) issue_loads(w, 0, bufs);
   cp_async_commit();
-  for (int it = 0; w < d.n_items; ++it, w += gridDim.x) {
-    const int cur = it & 1, nxt = cur ^ 1;
-    const int64_t wn = w + gridDim.x;
-    if (wn < d.n_items) item_info(wn, nxt);
-    __syncthreads();
-    if (wn < d.n_items) issue_loads(wn, nxt);
+  for (int it = 0; w < d.n_items; ++it, w += G0) {
+    const int ic = it % 3, in1 = (it + 1) % 3, in2 = (it + 2) % 3;
+    E* sm = bufs + ic * buf_elems;
+    // buffer (it + 1) % 3 was last read by item it - 2, finished before the
+    // previous iteration's barrier
+    if (w + G0 < d.n_items) issue_loads(w + G0, in1, bufs + in1 * buf_elems);
     cp_async_commit();
     cp_async_wait_prev();
     __syncthreads();
+    if (w + 2 * G0 < d.n_items) item_info(w + 2 * G0, in2);
 
-    E* sm = bufs + cur * buf_elems;
-    const unsigned tm = s_tmask[cur];
+    const unsigned tm = s_tmask[ic], vm = s_vmask[ic];
     if (tm) {   // upper slots arrive transposed but not yet conjugated
 #pragma unroll 1
       for (int slot = 0; slot < NSLOT; ++slot) {
         if (!((tm >> slot) & 1u)) continue;
         E* sbuf = sm + (slot << slot_log2);
-        for (int e = threadIdx.x; e < (1 << slot_log2); e += kMainThreads) sbuf[e] = P::conj_if(sbuf[e], 1u);
+#pragma unroll
+        for (int k = 0; k < ((1 << slot_log2) + kMainThreads - 1) / kMainThreads; ++k) {
+          const int e = int(threadIdx.x) + k * kMainThreads;
+          if ((1 << slot_log2) % kMainThreads == 0 || e < (1 << slot_log2)) sbuf[e] = P::conj_if(sbuf[e], 1u);
+        }
       }
       __syncthreads();
     }
     for (int o = 0; o < d.nops; ++o) {
       const PassOp& op = d.ops[o];
-      if (op.nq == 1) apply_1q<P, kMainThreads>(sm, gm, op, d.coef, rows_log2g, cols_log2g);
-      else if (op.kind == OP_U2) apply_u2_sep<P, kMainThreads>(sm, gm, op, d.coef, rows_log2g, cols_log2g);
-      else apply_ptm2<P, kMainThreads>(sm, gm, op, d.coef, rows_log2g, cols_log2g);
+      if (op.nq == 1) apply_1q<P, G, kMainThreads, rows_log2g, cols_log2g>(sm, gm, op, d.coef);
+      else if (!P2 || op.kind == OP_U2) apply_u2_sep<P, G, kMainThreads, rows_log2g, cols_log2g>(sm, gm, op, d.coef);
+      else if constexpr (P2) apply_ptm2<P, G, kMainThreads, rows_log2g, cols_log2g>(sm, gm, op, d.coef);
       __syncthreads();
     }
     // write back, each stored tile exactly once: lower slots as 16-byte row
     // granules, upper slots conjugated into their stored partner (skipped in
     // a diagonal group, where they mirror lower slots of the same group)
     const int r0 = int(w & chunk_mask) << rl;
+    const bool diag = s_diag[ic];
 #pragma unroll 1
     for (int slot = 0; slot < NSLOT; ++slot) {
-      const int64_t base = s_base[cur][slot];
+      if (!((vm >> slot) & 1u)) continue;
+      E* gbase = st + s_base[ic][slot];
       const E* sbuf = sm + (slot << slot_log2);
       if (!((tm >> slot) & 1u)) {
-        for (int g = threadIdx.x; g < (1 << (slot_log2 - GSH)); g += kMainThreads) {
-          const int within = g << GSH;
-          const int pr = within >> m, pc = within & (M - 1);
-          *reinterpret_cast<uint4*>(st + base + int64_t(r0 + pr) * M + pc) =
-              *reinterpret_cast<const uint4*>(sbuf + (pr << m) + (pc ^ ((pr & sw) << GSH)));
+        constexpr int NG = 1 << (slot_log2 - GSH);
+#pragma unroll
+        for (int k = 0; k < (NG + kMainThreads - 1) / kMainThreads; ++k) {
+          const int g = int(threadIdx.x) + k * kMainThreads;
+          if (NG % kMainThreads == 0 || g < NG) {
+            const int within = g << GSH;
+            const int pr = within >> m, pc = within & (M - 1);
+            *reinterpret_cast<uint4*>(gbase + (r0 + pr) * M + pc) =
+                *reinterpret_cast<const uint4*>(sbuf + (pr << m) + (pc ^ ((pr & sw) << GSH)));
+          }
         }
-      } else if (!s_diag[cur]) {
-        for (int e = threadIdx.x; e < (1 << slot_log2); e += kMainThreads) {
-          const int sr = e >> rl, sc = e & (R - 1);
-          st[base + int64_t(sr) * M + r0 + sc] = P::conj_if(sbuf[(sc << m) + (sr ^ ((sc & sw) << GSH))], 1u);
+      } else if (!diag) {
+        constexpr int NE = 1 << slot_log2;
+#pragma unroll
+        for (int k = 0; k < (NE + kMainThreads - 1) / kMainThreads; ++k) {
+          const int e = int(threadIdx.x) + k * kMainThreads;
+          if (NE % kMainThreads == 0 || e < NE) {
+            const int sr = e >> rl, sc = e & (R - 1);
+            gbase[sr * M + r0 + sc] = P::conj_if(sbuf[(sc << m) + (sr ^ ((sc & sw) << GSH))], 1u);
+          }
         }
       }
     }
-    __syncthreads();
   }
+  cp_async_wait_all();
 }
 
 // ------------------------------------------------------------------ diagonal groups
@@ -740,14 +804,19 @@ cudaError_t launch_one(void (*kfn)(E*, PassDesc), LaunchCache& lc, int threads, 
   return cudaGetLastError();
 }
 
-template <class P, int H>
+template <class P, int H, int MLOG, bool P2>
 cudaError_t launch_t(void* state, const PassDesc& d, cudaStream_t s, int* launches) {
   using E = typename P::Elem;
   constexpr int S_DIAG = (1 << H) * ((1 << H) + 1) / 2;   // stored slots of a diagonal group
+  // in-tile passes run packed on the one-high-qubit geometry (four tiles per item)
+  constexpr int HK = H == 0 ? 1 : H;
+  constexpr int RL = rows_log2_ct(HK, MLOG, int(sizeof(E)));
+  if (d.rows_log2 != RL || d.m != MLOG) return cudaErrorInvalidValue;
   static thread_local LaunchCache main_cache, diag_cache;
-  // two pipeline stages of one tile group each
-  const size_t smem = 2 * sizeof(E) * (size_t(1) << (2 * H + d.rows_log2 + d.m));
-  cudaError_t err = launch_one<E>(pass_kernel<P, H>, main_cache, kMainThreads, smem, d.n_items, state, d, s);
+  // three pipeline stages of one work item each
+  const size_t smem = 3 * sizeof(E) * (size_t(1) << (2 * HK + RL + MLOG));
+  cudaError_t err = launch_one<E>(pass_kernel<P, HK, MLOG, H == 0, P2>, main_cache, kMainThreads, smem,
+                                  d.n_items, state, d, s);
   if (err != cudaSuccess) return err;
   int n = d.n_items > 0 ? 1 : 0;
   // only two-high-qubit passes are row-chunked (tile_log2 <= 5)
@@ -764,26 +833,27 @@ cudaError_t launch_t(void* state, const PassDesc& d, cudaStream_t s, int* launch
   if (launches) *launches = n;
   return cudaSuccess;
 }
-template <class P>
+
+template <class P, int H, bool P2>
+cudaError_t launch_m(void* state, const PassDesc& d, cudaStream_t s, int* launches) {
+  switch (d.m) {
+    case 3: return launch_t<P, H, 3, P2>(state, d, s, launches);
+    case 4: return launch_t<P, H, 4, P2>(state, d, s, launches);
+    case 5: return launch_t<P, H, 5, P2>(state, d, s, launches);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class P, bool P2>
 cudaError_t launch_p(void* state, const PassDesc& d, cudaStream_t s, int* launches) {
+  if (launches) *launches = 0;
   switch (d.h) {
-    case 0: return launch_t<P, 0>(state, d, s, launches);
-    case 1: return launch_t<P, 1>(state, d, s, launches);
-    case 2: return launch_t<P, 2>(state, d, s, launches);
+    case 0: return launch_m<P, 0, P2>(state, d, s, launches);
+    case 1: return launch_m<P, 1, P2>(state, d, s, launches);
+    case 2: return launch_m<P, 2, P2>(state, d, s, launches);
   }
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
-
-cudaError_t launch_pass(int dtype, void* state, const PassDesc& d, cudaStream_t s, int* launches) {
-  if (launches) *launches = 0;
-  switch (dtype) {
-    case DT_C128: return launch_p<PolF64>(state, d, s, launches);
-    case DT_C64: return launch_p<PolF32>(state, d, s, launches);
-    case DT_DF64: return launch_p<PolDF64>(state, d, s, launches);
-  }
-  return cudaErrorInvalidValue;
-}
-
 }  // namespace orkan

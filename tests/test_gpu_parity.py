@@ -76,7 +76,7 @@ def _single_ops(n, rng):
     return ops
 
 
-CASES = [(n, 5) for n in range(1, 9)] + [(6, 2), (7, 3), (8, 3), (7, 4), (9, 2)]
+CASES = [(n, 5) for n in range(1, 9)] + [(6, 3), (7, 3), (8, 3), (7, 4), (9, 3), (9, 4)]
 
 
 @pytest.mark.parametrize("dtype", ["c128", "df64", "c64"])
@@ -144,7 +144,7 @@ def test_config0_circuit_n8(dtype, fusion):
 
 # ------------------------------------------------------------------ fused passes (h = 0, 1, 2 with low ops)
 @pytest.mark.parametrize("dtype", ["c128", "df64", "c64"])
-@pytest.mark.parametrize("n,m", [(8, 3), (9, 4), (7, 5), (10, 2)])
+@pytest.mark.parametrize("n,m", [(8, 3), (9, 4), (7, 5), (10, 3)])
 def test_fused_random_circuit(n, m, dtype):
     rng = S.rng_for(2000 + n + 10 * m)
     rho0 = S.ginibre_state(rng, 1 << n)
@@ -198,7 +198,7 @@ def test_chunked_high_pairs(n, dtype):
 
 # ------------------------------------------------------------------ init kinds and layout
 @pytest.mark.parametrize("dtype", ["c128", "df64", "c64"])
-@pytest.mark.parametrize("n,m", [(1, 5), (3, 2), (5, 5), (7, 3), (9, 5)])
+@pytest.mark.parametrize("n,m", [(1, 5), (3, 3), (5, 5), (7, 3), (9, 5)])
 def test_init_kinds_and_layout(n, m, dtype):
     rng = S.rng_for(3000 + n * 7 + m)
     N = 1 << n
@@ -232,7 +232,7 @@ def test_init_kinds_and_layout(n, m, dtype):
 
 # ------------------------------------------------------------------ readouts
 @pytest.mark.parametrize("dtype", ["c128", "df64", "c64"])
-@pytest.mark.parametrize("n,m", [(1, 5), (3, 2), (6, 5), (8, 3), (10, 5)])
+@pytest.mark.parametrize("n,m", [(1, 5), (3, 3), (6, 5), (8, 3), (10, 5)])
 def test_readouts(n, m, dtype):
     rng = S.rng_for(4000 + n + m)
     N = 1 << n
