@@ -54,6 +54,9 @@ def parse_args(argv=None):
     p.add_argument("--no-variants", action="store_true", help="skip the c128 / c64 / unfused comparison runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=20.0)
+    p.add_argument("--workload", choices=["sweep", "serving"], default="sweep")
+    p.add_argument("--serve-requests", type=int, default=160,
+                   help="requests in the serving sample of the default run (the serving workload uses 5000)")
     p.add_argument("--op-class", default=None,
                    help="time only single-op passes of one class (u1_in, u2_in_cross, ...) and print their GB/s")
     return p.parse_args(argv)
@@ -279,6 +282,31 @@ def per_op_table(ok, wl, n, m, dtypes, stream, torch, reps=4, only=None):
     return out
 
 
+def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=True):
+    """Continuous batching vs one-at-a-time plain FP64 on the same requests.
+    Capacity: all requests present at t = 0; latency runs: Poisson arrivals at
+    a fraction of the measured capacity (arrival times rescaled)."""
+    from paper_2604_15765_gb300 import serving
+    served_map = {"c128": "df64"}
+    out = {"requests": len(reqs), "slots": slots, "memory_budget_bytes": budget,
+           "served_form": "8 concurrent slots, c128 requests in df64, fused passes (8 ops, composed)"}
+    _, cap = serving.serve(reqs, budget, slots=slots, dtype_map=served_map, realtime=False)
+    out["served_capacity"] = cap
+    base_t = [r["t"] for r in reqs]
+    for frac in realtime_fracs:
+        rate = frac * cap["solves_per_s"]
+        span = base_t[-1] if base_t[-1] > 0 else 1.0
+        scaled = [dict(r, t=r["t"] * (len(reqs) / rate) / span) for r in reqs]
+        _, st = serving.serve(scaled, budget, slots=slots, dtype_map=served_map, realtime=True)
+        out[f"served_at_{frac:.1f}x_capacity"] = st
+    if baseline:
+        _, b = serving.serve(reqs, budget, slots=1, dtype_map={"c64": "c128"}, fusion=1, compose=False,
+                             realtime=False)
+        out["plain_fp64_one_at_a_time"] = b
+    torch.cuda.synchronize()
+    return out
+
+
 def time_steps(runner, steps, warmup, torch):
     for _ in range(warmup):
         runner.step()
@@ -388,6 +416,20 @@ def main(argv=None):
         tab = per_op_table(ok, wl, n, m, (args.dtype,), stream, torch, reps=args.steps, only=args.op_class)
         print(json.dumps({"op_class": args.op_class, "dtype": args.dtype, "n": n, "pass_GBps": tab[args.dtype]}))
         return 0
+    if args.workload == "serving":
+        from workloads import synth as S
+        reqs = S.serving_stream(count=5000)
+        st = serving_study(reqs, torch, budget=64 << 30, realtime_fracs=(0.5, 0.9, 1.2))
+        cap = st["served_capacity"]
+        line = {"metric": METRIC, "value": round(cap["ops_per_s"], 2), "unit": UNIT, "n_gpus": world, "steps": 1,
+                "warmup": 0, "ms_per_step": round(cap["elapsed_s"] * 1e3, 1), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "c128/c64 requests (c128 served in df64)",
+                "data": "synthetic",
+                "config": {"workload": "serving: 5000 seeded requests, n~U{4..14}, depth~U{10..200} from the "
+                                       "mixed op mix, 50/50 picture and dtype"},
+                "serving": st}
+        print(json.dumps(line), flush=True)
+        return 0
     compose = not args.no_compose
     runner = Runner(ok, circuit, wl, n, m, args.dtype, args.fusion, compose, stream)
 
@@ -454,8 +496,11 @@ def main(argv=None):
             r.free()
 
     per_op = None
+    serving_res = None
     if not args.no_variants and world == 1:
         per_op = per_op_table(ok, wl, n, m, ("df64", "c128", "c64"), stream, torch)
+        from workloads import synth as S
+        serving_res = serving_study(S.serving_stream(count=args.serve_requests), torch, budget=32 << 30)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -481,6 +526,7 @@ def main(argv=None):
             "clocks": clocks,
             "variants": variants,
             "per_op_pass_GBps": per_op,
+            "serving": serving_res,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -191,6 +191,8 @@ struct orkan_ctx {
   double* d_partials = nullptr;
   double* d_res = nullptr;
   double* h_res = nullptr;   // pinned
+  void* d_upload = nullptr;  // grow-only staging buffer for init uploads (no per-call cudaMalloc/cudaFree,
+  size_t upload_cap = 0;     // which could synchronise the device under concurrent requests)
   int64_t n_passes = 0, n_ops = 0, n_launches = 0;
   bool timing = false;
   std::vector<cudaEvent_t> ev_free;
@@ -425,6 +427,28 @@ HostOp make_ad_op(int q, const double R[16]) {
   return op;
 }
 
+// Device staging space of at least `bytes` for host uploads, kept for the
+// handle's lifetime; earlier uploads are stream-ordered before later ones.
+int upload_space(orkan_ctx* h, size_t bytes, void** out) {
+  if (bytes > h->upload_cap) {
+    if (h->d_upload) {
+      cudaError_t e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "upload_space");
+      cudaFree(h->d_upload);
+      h->d_upload = nullptr;
+      h->upload_cap = 0;
+    }
+    size_t cap = bytes < 4096 ? 4096 : bytes;
+    if (cudaMalloc(&h->d_upload, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ORKAN_ENOMEM, "cudaMalloc(upload staging) failed");
+    }
+    h->upload_cap = cap;
+  }
+  *out = h->d_upload;
+  return ORKAN_OK;
+}
+
 int reduce_diag(orkan_ctx* h, int q, double out[4]) {
   int st = flush_pending(h);
   if (st != ORKAN_OK) return st;
@@ -455,6 +479,7 @@ void release_handle(orkan_ctx* c) {
   }
   for (auto e : c->ev_free) cudaEventDestroy(e);
   if (c->d_state && !c->external) cudaFree(c->d_state);
+  if (c->d_upload) cudaFree(c->d_upload);
   if (c->d_partials) cudaFree(c->d_partials);
   if (c->d_res) cudaFree(c->d_res);
   if (c->h_res) cudaFreeHost(c->h_res);
@@ -647,18 +672,13 @@ int orkan_init_state(orkan_h h, int kind, const double* data) {
     case ORKAN_INIT_PURE: {
       if (!data) return fail(ORKAN_EINVAL, "data required");
       const size_t count = kind == ORKAN_INIT_DENSE ? size_t(h->g.N) * size_t(h->g.N) : size_t(h->g.N);
-      double* tmp = nullptr;
-      if (cudaMalloc(&tmp, count * 16) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ORKAN_ENOMEM, "cudaMalloc(upload) failed");
-      }
-      cudaError_t e = cudaMemcpyAsync(tmp, data, count * 16, cudaMemcpyHostToDevice, h->stream);
-      if (e == cudaSuccess)
-        e = kind == ORKAN_INIT_DENSE ? launch_from_dense(h->dtype, h->d_state, h->g, tmp, h->stream)
-                                     : launch_from_pure(h->dtype, h->d_state, h->g, tmp, h->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-      cudaFree(tmp);
-      if (e != cudaSuccess) return cuda_fail(e, "init_state");
+      void* tmp = nullptr;
+      if (int st = upload_space(h, count * 16, &tmp)) return st;
+      ORKAN_CUDA(cudaMemcpyAsync(tmp, data, count * 16, cudaMemcpyHostToDevice, h->stream));
+      if (kind == ORKAN_INIT_DENSE)
+        ORKAN_CUDA(launch_from_dense(h->dtype, h->d_state, h->g, static_cast<const double*>(tmp), h->stream));
+      else
+        ORKAN_CUDA(launch_from_pure(h->dtype, h->d_state, h->g, static_cast<const double*>(tmp), h->stream));
       h->n_launches += 1;
       return ORKAN_OK;
     }
@@ -700,20 +720,16 @@ int orkan_init_observable(orkan_h h, int nterms, const char* paulis, const doubl
     masks.insert(masks.end(), {t.x, t.z, t.y, t.ny});
     cs.push_back(t.c);
   }
-  uint64_t* dm = nullptr;
-  double* dc = nullptr;
-  if (cudaMalloc(&dm, masks.size() * 8) != cudaSuccess || cudaMalloc(&dc, cs.size() * 8) != cudaSuccess) {
-    cudaGetLastError();
-    if (dm) cudaFree(dm);
-    return fail(ORKAN_ENOMEM, "cudaMalloc(pauli terms) failed");
-  }
-  cudaError_t e = cudaMemcpyAsync(dm, masks.data(), masks.size() * 8, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dc, cs.data(), cs.size() * 8, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = launch_pauli_sum(h->dtype, h->d_state, h->g, int(terms.size()), dm, dc, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(dm);
-  cudaFree(dc);
-  if (e != cudaSuccess) return cuda_fail(e, "init_observable");
+  void* stage = nullptr;
+  const size_t mbytes = masks.size() * 8, cbytes = cs.size() * 8;
+  if (int st = upload_space(h, mbytes + cbytes, &stage)) return st;
+  uint64_t* dm = static_cast<uint64_t*>(stage);
+  double* dc = reinterpret_cast<double*>(static_cast<char*>(stage) + mbytes);
+  ORKAN_CUDA(cudaMemcpyAsync(dm, masks.data(), mbytes, cudaMemcpyHostToDevice, h->stream));
+  ORKAN_CUDA(cudaMemcpyAsync(dc, cs.data(), cbytes, cudaMemcpyHostToDevice, h->stream));
+  // masks / cs are host temporaries: the copies must have read them before return
+  ORKAN_CUDA(launch_pauli_sum(h->dtype, h->d_state, h->g, int(terms.size()), dm, dc, h->stream));
+  ORKAN_CUDA(cudaStreamSynchronize(h->stream));
   h->n_launches += 1;
   return ORKAN_OK;
 }

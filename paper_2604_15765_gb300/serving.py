@@ -1,0 +1,167 @@
+"""Request serving over the Orkan C ABI: continuous batching of mixed-size simulations.
+
+A request (from ``workloads.synth.serving_stream``) is one circuit on one
+operator:
+  * Schroedinger: start from a product state rho0, apply the circuit (unitaries,
+    channels, Z measurements with the request's draws), return 8 Pauli-string
+    expectations;
+  * Heisenberg: start from a 16-term Pauli-sum observable O, apply the adjoint
+    circuit in reverse order, return tr(O rho0) for the request's product
+    state rho0.
+
+The server keeps every operator resident in HBM (handles are pooled per
+(n, dtype) and reused), admits a request once it has arrived and its packed
+tile bytes fit the memory budget, and runs admitted requests concurrently:
+each of ``slots`` worker threads owns its own handles and therefore its own
+CUDA streams, so the passes of different requests overlap on the GPU while
+new requests are admitted as slots and memory free up.  The Python layer only
+issues C-ABI calls (ctypes releases the interpreter lock during each call);
+every step of every circuit runs in the library's kernels.
+
+Results are deterministic per request: each kernel's grid and reduction order
+depend only on the request's own operator, never on what else is running.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+
+import numpy as np
+
+from . import circuit
+from . import orkan as ok
+
+DT = {"c128": ok.ORKAN_C128, "c64": ok.ORKAN_C64, "df64": ok.ORKAN_DF64}
+
+
+class HandlePool:
+    """Resident operators per (n, dtype, tile_log2), with memory accounting."""
+
+    def __init__(self, budget_bytes: int, tile_log2: int = 5):
+        self.budget = int(budget_bytes)
+        self.m = tile_log2
+        self.free = collections.defaultdict(list)
+        self.allocated = 0
+        self.lock = threading.Lock()
+        self.cv = threading.Condition(self.lock)
+
+    def nbytes(self, n, dtype):
+        return ok.orkan_bytes(n, DT[dtype], self.m)
+
+    def _evict_idle(self, need):
+        for key in list(self.free):
+            while self.free[key] and self.allocated + need > self.budget:
+                h = self.free[key].pop()
+                ok.orkan_free(h)
+                self.allocated -= self.nbytes(key[0], key[1])
+
+    def acquire(self, n, dtype, count=1, block=True):
+        """count handles for an n-qubit operator, or None if not admissible now."""
+        need_each = self.nbytes(n, dtype)
+        with self.cv:
+            while True:
+                reuse = min(count, len(self.free[(n, dtype)]))
+                need = need_each * (count - reuse)
+                if self.allocated + need > self.budget:
+                    self._evict_idle(need)
+                if self.allocated + need <= self.budget:
+                    hs = [self.free[(n, dtype)].pop() for _ in range(reuse)]
+                    for _ in range(count - reuse):
+                        hs.append(ok.orkan_alloc(n, DT[dtype], self.m))
+                        self.allocated += need_each
+                    return hs
+                if not block:
+                    return None
+                self.cv.wait(timeout=0.05)
+
+    def release(self, n, dtype, hs):
+        with self.cv:
+            self.free[(n, dtype)].extend(hs)
+            self.cv.notify_all()
+
+    def close(self):
+        with self.cv:
+            for key, hs in self.free.items():
+                for h in hs:
+                    ok.orkan_free(h)
+            self.free.clear()
+            self.allocated = 0
+
+
+def run_request(pool: HandlePool, req, dtype_map=None, fusion=8, compose=True):
+    """Execute one request on pooled handles; returns its result vector."""
+    dtype = (dtype_map or {}).get(req["dtype"], req["dtype"])
+    n = req["n"]
+    if req["picture"] == "schrodinger":
+        (h,) = pool.acquire(n, dtype, 1)
+        try:
+            ok.orkan_set_fusion(h, fusion, compose)
+            ok.orkan_init_state(h, ok.ORKAN_INIT_PURE, req["psi0"])
+            circuit.run_circuit(h, req["ops"], "schrodinger")
+            out = np.array([ok.orkan_expect_pauli(h, s) for s in req["paulis"]])
+        finally:
+            pool.release(n, dtype, [h])
+        return out
+    hO, h0 = pool.acquire(n, dtype, 2)
+    try:
+        ok.orkan_set_fusion(hO, fusion, compose)
+        ok.orkan_init_observable(hO, req["paulis"], req["coeffs"])
+        circuit.run_circuit(hO, list(reversed(req["ops"])), "heisenberg")
+        ok.orkan_init_state(h0, ok.ORKAN_INIT_PURE, req["psi0"])
+        out = np.array([ok.orkan_expect(h0, hO)])
+    finally:
+        pool.release(n, dtype, [hO, h0])
+    return out
+
+
+def serve(requests, budget_bytes, slots=8, dtype_map=None, fusion=8, compose=True, realtime=True,
+          tile_log2=5):
+    """Continuous batching: requests become eligible at their arrival time
+    (offsets from the start when ``realtime``), are admitted in arrival order
+    when a slot is free and their bytes fit the budget, and run concurrently.
+    Returns (results by request id, stats)."""
+    pool = HandlePool(budget_bytes, tile_log2)
+    order = sorted(requests, key=lambda r: r["t"])
+    nxt = [0]
+    qlock = threading.Lock()
+    results, lat = {}, {}
+    errors = []
+    t0 = time.perf_counter()
+
+    def worker():
+        while True:
+            with qlock:
+                if nxt[0] >= len(order):
+                    return
+                req = order[nxt[0]]
+                nxt[0] += 1
+            if realtime:
+                wait = req["t"] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+            arrival = t0 + req["t"] if realtime else t0
+            try:
+                res = run_request(pool, req, dtype_map, fusion, compose)
+            except Exception as e:  # noqa: BLE001  (reported to the caller)
+                errors.append((req["id"], repr(e)))
+                continue
+            done = time.perf_counter()
+            results[req["id"]] = res
+            lat[req["id"]] = done - arrival
+
+    threads = [threading.Thread(target=worker, daemon=True) for _ in range(slots)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    elapsed = time.perf_counter() - t0
+    pool.close()
+    if errors:
+        raise RuntimeError(f"{len(errors)} requests failed, first: {errors[0]}")
+    lv = np.array(sorted(lat.values())) if lat else np.zeros(1)
+    ops = sum(len(r["ops"]) for r in requests)
+    stats = {"requests": len(results), "elapsed_s": elapsed, "solves_per_s": len(results) / elapsed,
+             "ops_per_s": ops / elapsed, "p50_ms": float(np.percentile(lv, 50) * 1e3),
+             "p99_ms": float(np.percentile(lv, 99) * 1e3), "slots": slots}
+    return results, stats
