@@ -32,6 +32,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -54,7 +56,8 @@ def parse_args(argv=None):
     p.add_argument("--no-variants", action="store_true", help="skip the c128 / c64 / unfused comparison runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=20.0)
-    p.add_argument("--workload", choices=["sweep", "serving"], default="sweep")
+    p.add_argument("--workload", choices=["sweep", "serving", "brickwork", "precision"], default="sweep")
+    p.add_argument("--depth", type=int, default=40)
     p.add_argument("--serve-requests", type=int, default=160,
                    help="requests in the serving sample of the default run (the serving workload uses 5000)")
     p.add_argument("--op-class", default=None,
@@ -307,6 +310,133 @@ def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=
     return out
 
 
+def _run_timed(ok, circuit, torch, stream, n, dt, m, fusion, compose, ops, paulis, psi):
+    """One operator through ops, then the Pauli strings; device time, pass stats, handle."""
+    h = ok.orkan_alloc(n, DTYPE_NAMES[dt], m)
+    ok.orkan_set_stream(h, stream)
+    ok.orkan_set_fusion(h, fusion, compose)
+    ok.orkan_init_state(h, ok.ORKAN_INIT_PURE, psi)
+    ok.orkan_sync(h)
+    ok.orkan_set_timing(h, True)
+    ok.orkan_pass_time(h)
+    p0 = ok.orkan_stats(h)["passes"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for op in ops:
+        circuit.apply_op(h, op)
+    ok.orkan_flush(h)
+    ev1.record()
+    exps = np.array([ok.orkan_expect_pauli(h, s) for s in paulis])
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    pass_ms, cnt = ok.orkan_pass_time(h)
+    ok.orkan_set_timing(h, False)
+    nb = 2 * ok.orkan_bytes(n, DTYPE_NAMES[dt], m)
+    st = {"ops_per_s": round(len(ops) / (ms / 1e3), 1), "ms": round(ms, 1), "passes": ok.orkan_stats(h)["passes"] - p0,
+          "tile_log2": m, "fusion": fusion, "compose": compose,
+          "avg_pass_GBps": round(nb / (pass_ms / max(cnt, 1) * 1e-3) / 1e9, 1),
+          "avg_pass_hbm_frac": round(nb / (pass_ms / max(cnt, 1) * 1e-3) / 1e9 / peaks()[0], 4),
+          "trace_error": abs(ok.orkan_trace(h) - 1.0)}
+    return h, st, exps
+
+
+def brickwork_study(ok, circuit, torch, stream, n, dt, depth):
+    """Layered noisy brickwork (Haar 1q on all qubits, Haar 2q on alternating
+    pairs, depolarising 1e-3 on all), autotuned tile size and fusion depth
+    against the unfused schedule (m = 5, one pass per op), 32 Pauli strings."""
+    from workloads import synth as S
+    rng = S.rng_for(S.BASE_SEED + 2)
+    psi = S.haar_state_vector(rng, 1 << n)
+    paulis = S.random_pauli_strings(rng, n, 32)
+    ops = S.brickwork(n, depth)
+    t0 = time.perf_counter()
+    m, f = ok.orkan_autotune(n, DTYPE_NAMES[dt])
+    tune_s = time.perf_counter() - t0
+    out = {"n": n, "dtype": dt, "depth": depth, "ops": len(ops), "autotune_s": round(tune_s, 2)}
+    res = {}
+    for label, (mm, ff, cc) in (("autotuned", (m, f, True)), ("unfused", (5, 1, False))):
+        h, st, ex = _run_timed(ok, circuit, torch, stream, n, dt, mm, ff, cc, ops, paulis, psi)
+        ok.orkan_free(h)
+        out[label] = st
+        res[label] = ex
+    out["max_expectation_diff_tuned_vs_unfused"] = float(np.max(np.abs(res["autotuned"] - res["unfused"])))
+    out["speedup_tuned_over_unfused"] = round(out["autotuned"]["ops_per_s"] / out["unfused"]["ops_per_s"], 2)
+    return out
+
+
+def precision_study(ok, circuit, torch, stream, depth):
+    """Trace distance / max |delta| / Frobenius / trace error of the storage
+    and arithmetic forms on the depth-40 noisy brickwork: against the CPU
+    oracle at n = 10, against the GPU complex128 run at n = 12 and n = 16, and
+    against the GPU double-float run at n = 17 (complex64 only otherwise)."""
+    from oracle import dense as D
+    from workloads import synth as S
+    out = {}
+
+    def states(n, dts, m=5):
+        rng = S.rng_for(S.BASE_SEED + 3)
+        psi = S.haar_state_vector(rng, 1 << n)
+        ops = S.brickwork(n, depth, seed=S.BASE_SEED + 3)
+        return psi, ops
+
+    # n = 10: every form against the oracle (dense, CPU)
+    n = 10
+    psi, ops = states(n, None)
+    t0 = time.perf_counter()
+    ref, _ = D.run_circuit(np.outer(psi, psi.conj()), ops)
+    cpu_s = time.perf_counter() - t0
+    row = {"oracle_cpu_s": round(cpu_s, 1)}
+    for dt in ("c128", "df64", "c64"):
+        h, st, _ = _run_timed(ok, circuit, torch, stream, n, dt, 5, 8, True, ops, [], psi)
+        got = ok.orkan_to_dense(h)
+        ok.orkan_free(h)
+        row[dt] = {"max_abs": D.max_abs_diff(got, ref), "frobenius": D.frobenius_diff(got, ref),
+                   "trace_distance": D.trace_distance(got, ref), "trace_error": st["trace_error"]}
+    out["n10_vs_oracle"] = row
+    # n = 12: df64 and c64 against the GPU complex128 run (dense download, exact trace distance)
+    n = 12
+    psi, ops = states(n, None)
+    dense = {}
+    for dt in ("c128", "df64", "c64"):
+        h, st, _ = _run_timed(ok, circuit, torch, stream, n, dt, 5, 8, True, ops, [], psi)
+        dense[dt] = (ok.orkan_to_dense(h), st)
+        ok.orkan_free(h)
+    row = {}
+    for dt in ("df64", "c64"):
+        a, b = dense[dt][0], dense["c128"][0]
+        row[dt] = {"max_abs": D.max_abs_diff(a, b), "frobenius": D.frobenius_diff(a, b),
+                   "trace_distance": D.trace_distance(a, b), "trace_error": dense[dt][1]["trace_error"]}
+    row["c128_trace_error"] = dense["c128"][1]["trace_error"]
+    out["n12_vs_gpu_c128"] = row
+    del dense
+    # n = 16 (c128 reference) and n = 17 (df64 reference): sampled elements
+    for n, refdt, dts in ((16, "c128", ("df64", "c64")), (17, "df64", ("c64",))):
+        psi, ops = states(n, None)
+        rng = S.rng_for(99 + n)
+        N = 1 << n
+        rows_i = rng.integers(0, N, 1 << 20)
+        cols_i = rng.integers(0, N, 1 << 20)
+        diag_i = rng.integers(0, N, 1 << 16)
+        rows_i = np.concatenate([rows_i, diag_i])
+        cols_i = np.concatenate([cols_i, diag_i])
+        h, st_ref, _ = _run_timed(ok, circuit, torch, stream, n, refdt, 5, 8, True, ops, [], psi)
+        ref_s = ok.orkan_get_elements(h, rows_i, cols_i)
+        ok.orkan_free(h)
+        row = {"reference": refdt, "reference_ops_per_s": st_ref["ops_per_s"], "sampled_elements": int(rows_i.size),
+               "reference_trace_error": st_ref["trace_error"]}
+        for dt in dts:
+            h, st, _ = _run_timed(ok, circuit, torch, stream, n, dt, 5, 8, True, ops, [], psi)
+            got = ok.orkan_get_elements(h, rows_i, cols_i)
+            ok.orkan_free(h)
+            d = got - ref_s
+            row[dt] = {"max_abs_sampled": float(np.max(np.abs(d))),
+                       "frobenius_estimate": float(np.sqrt(np.mean(np.abs(d) ** 2)) * N),
+                       "trace_distance_bound": float(np.sqrt(np.mean(np.abs(d) ** 2)) * N * np.sqrt(N)),
+                       "trace_error": st["trace_error"], "ops_per_s": st["ops_per_s"]}
+        out[f"n{n}_vs_gpu_{refdt}"] = row
+    return out
+
+
 def time_steps(runner, steps, warmup, torch):
     for _ in range(warmup):
         runner.step()
@@ -415,6 +545,25 @@ def main(argv=None):
     if args.op_class:
         tab = per_op_table(ok, wl, n, m, (args.dtype,), stream, torch, reps=args.steps, only=args.op_class)
         print(json.dumps({"op_class": args.op_class, "dtype": args.dtype, "n": n, "pass_GBps": tab[args.dtype]}))
+        return 0
+    if args.workload in ("brickwork", "precision"):
+        import numpy  # noqa: F401
+        if args.workload == "brickwork":
+            bw = brickwork_study(ok, circuit, torch, stream, 16 if args.n == 14 else args.n, args.dtype, args.depth)
+            val = bw["autotuned"]["ops_per_s"]
+            cfg = {"workload": f"noisy brickwork n={bw['n']}, depth {args.depth}, autotuned vs unfused",
+                   "n": bw["n"], "depth": args.depth}
+            extra = {"brickwork": bw}
+        else:
+            pr = precision_study(ok, circuit, torch, stream, args.depth)
+            val = pr["n16_vs_gpu_c128"]["df64"]["ops_per_s"]
+            cfg = {"workload": f"precision study: noisy brickwork depth {args.depth} at n=10/12/16/17"}
+            extra = {"precision": pr}
+        line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 0,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+                "data": "synthetic", "config": cfg}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
         return 0
     if args.workload == "serving":
         from workloads import synth as S

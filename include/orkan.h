@@ -137,6 +137,17 @@ int orkan_set_fusion(orkan_h h, int max_ops, int compose);
 
 int orkan_get_info(orkan_h h, int *n, int *dtype, int *tile_log2, int *picture);
 
+/* Autotuner: the tile size (tile_log2, 3..5) and fusion depth (max_ops,
+ * 1..16, with composition) that run a noisy brickwork probe fastest on the
+ * current device for n-qubit operators of dtype.  It times one warm-up and two
+ * probe layers (a 1-qubit gate on every qubit, 2-qubit gates on alternating
+ * neighbour pairs, depolarising on every qubit) on min(n, 13) qubits for every
+ * candidate pair, allocating and freeing temporary operators.  The choice is
+ * cached per (device, n, dtype) for the process and, when the environment
+ * variable ORKAN_TUNE_CACHE names a file, read from / appended to it.
+ * Errors: EINVAL, ENODEV, ENOMEM, ECUDA.  (Not in the paper, which fixes m = 5.) */
+int orkan_autotune(int n, int dtype, int *tile_log2, int *max_ops);
+
 /* Device address of the tiled array (layout of Sec. III-B, element type of the dtype). */
 void *orkan_device_ptr(orkan_h h);
 

@@ -9,6 +9,12 @@
 // then one read and one write of the tiled array.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <tuple>
 #include <complex>
 #include <cstdio>
 #include <cstring>
@@ -987,3 +993,144 @@ int orkan_pass_time(orkan_h h, double* ms, int64_t* count) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ autotuner
+namespace {
+
+// Fixed probe gates: Rz(a) Ry(b) Rz(c) and CNOT (Ry x Rz), row-major complex128.
+void probe_u1(int q, double out[8]) {
+  const double a = 0.37 + 0.11 * q, b = 1.1 + 0.07 * q, c = -0.29 + 0.05 * q;
+  const cd e1 = std::exp(cd(0, -(a + c) / 2)), e2 = std::exp(cd(0, -(a - c) / 2));
+  const cd u00 = e1 * std::cos(b / 2), u01 = -std::conj(e2) * std::sin(b / 2);
+  const cd u10 = e2 * std::sin(b / 2), u11 = std::conj(e1) * std::cos(b / 2);
+  const cd u[4] = {u00, u01, u10, u11};
+  for (int i = 0; i < 4; ++i) { out[2 * i] = u[i].real(); out[2 * i + 1] = u[i].imag(); }
+}
+void probe_u2(double out[32]) {
+  double a[8], b[8];
+  probe_u1(1, a);
+  probe_u1(2, b);
+  Mat A(4), B(4), AB(16), C(16, 0.0);
+  for (int i = 0; i < 4; ++i) { A[i] = cd(a[2 * i], a[2 * i + 1]); B[i] = cd(b[2 * i], b[2 * i + 1]); }
+  for (int i = 0; i < 4; ++i)   // kron(B, A): bit 0 <-> A
+    for (int j = 0; j < 4; ++j) AB[i * 4 + j] = B[(i >> 1) * 2 + (j >> 1)] * A[(i & 1) * 2 + (j & 1)];
+  const int perm[4] = {0, 3, 2, 1};   // CNOT, control = index bit 0
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) C[perm[i] * 4 + j] = AB[i * 4 + j];
+  for (int i = 0; i < 16; ++i) { out[2 * i] = C[i].real(); out[2 * i + 1] = C[i].imag(); }
+}
+
+// One noisy brickwork layer: 1q gate on every qubit, 2q gate on alternating
+// neighbour pairs, depolarising on every qubit.
+int probe_layer(orkan_h h, int n, int parity) {
+  double u1[8], u2[32];
+  probe_u2(u2);
+  for (int q = 0; q < n; ++q) {
+    probe_u1(q, u1);
+    if (int st = orkan_apply_unitary(h, 1, &q, u1)) return st;
+  }
+  for (int q = parity; q + 1 < n; q += 2) {
+    const int qs[2] = {q, q + 1};
+    if (int st = orkan_apply_unitary(h, 2, qs, u2)) return st;
+  }
+  for (int q = 0; q < n; ++q)
+    if (int st = orkan_depolarize(h, q, 1e-3)) return st;
+  return ORKAN_OK;
+}
+
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune_cache;
+
+std::string device_name(int dev) {
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+  std::string s = p.name;
+  std::replace(s.begin(), s.end(), ' ', '_');
+  return s;
+}
+
+}  // namespace
+
+extern "C" int orkan_autotune(int n, int dtype, int* tile_log2, int* max_ops) {
+  Geometry g;
+  if (!tile_log2 || !max_ops || !valid_dtype(dtype) || !geometry(n, 5, &g))
+    return fail(ORKAN_EINVAL, "bad autotune arguments");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(ORKAN_ENODEV, "no CUDA device");
+  const auto key = std::make_tuple(dev, n, dtype);
+  const std::string gpu = device_name(dev);
+  const char* path = std::getenv("ORKAN_TUNE_CACHE");
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      *tile_log2 = it->second.first;
+      *max_ops = it->second.second;
+      return ORKAN_OK;
+    }
+    if (path) {
+      std::ifstream f(path);
+      std::string name;
+      int fn, fd, fm, ff;
+      while (f >> name >> fn >> fd >> fm >> ff) {
+        if (name == gpu && fn == n && fd == dtype) {
+          g_tune_cache[key] = {fm, ff};
+          *tile_log2 = fm;
+          *max_ops = ff;
+          return ORKAN_OK;
+        }
+      }
+    }
+  }
+  const int np = std::min(n, 13);
+  const int layers = 2;
+  float best = 1e30f;
+  int best_m = 5, best_f = 8;
+  cudaEvent_t e0, e1;
+  ORKAN_CUDA(cudaEventCreate(&e0));
+  ORKAN_CUDA(cudaEventCreate(&e1));
+  for (int m = 3; m <= 5; ++m) {
+    for (int f : {1, 2, 4, 8, 16}) {
+      orkan_h h = nullptr;
+      int st = orkan_alloc(np, dtype, m, &h);
+      if (st != ORKAN_OK) continue;
+      st = orkan_init_state(h, ORKAN_INIT_MAXMIXED, nullptr);
+      if (st == ORKAN_OK) st = orkan_set_fusion(h, f, 1);
+      if (st == ORKAN_OK) st = probe_layer(h, np, 0);   // warm-up: kernels loaded, caches set
+      if (st == ORKAN_OK) st = orkan_sync(h);
+      float ms = 0.0f;
+      if (st == ORKAN_OK) {
+        cudaEventRecord(e0, h->stream);
+        for (int l = 0; l < layers && st == ORKAN_OK; ++l) st = probe_layer(h, np, l & 1);
+        if (st == ORKAN_OK) st = orkan_flush(h);
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+          st = ORKAN_ECUDA;
+      }
+      orkan_free(h);
+      if (st != ORKAN_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+      }
+      if (ms < best) {
+        best = ms;
+        best_m = m;
+        best_f = f;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = {best_m, best_f};
+    if (path) {
+      std::ofstream f(path, std::ios::app);
+      f << gpu << ' ' << n << ' ' << dtype << ' ' << best_m << ' ' << best_f << '\n';
+    }
+  }
+  *tile_log2 = best_m;
+  *max_ops = best_f;
+  return ORKAN_OK;
+}

@@ -52,6 +52,7 @@ _SIGS = {
     "orkan_set_stream": (C.c_int, [_h, C.c_void_p]),
     "orkan_set_fusion": (C.c_int, [_h, C.c_int, C.c_int]),
     "orkan_get_info": (C.c_int, [_h, _pi, _pi, _pi, _pi]),
+    "orkan_autotune": (C.c_int, [C.c_int, C.c_int, _pi, _pi]),
     "orkan_device_ptr": (C.c_void_p, [_h]),
     "orkan_init_state": (C.c_int, [_h, C.c_int, _pd]),
     "orkan_init_observable": (C.c_int, [_h, C.c_int, C.c_char_p, _pd]),
@@ -163,6 +164,13 @@ def orkan_get_info(h):
     v = [C.c_int() for _ in range(4)]
     _check(_lib.orkan_get_info(h, *[C.byref(x) for x in v]), "orkan_get_info")
     return tuple(x.value for x in v)
+
+
+def orkan_autotune(n: int, dtype: int):
+    """(tile_log2, max_ops) chosen by the library's autotuner for this device."""
+    m, f = C.c_int(), C.c_int()
+    _check(_lib.orkan_autotune(n, dtype, C.byref(m), C.byref(f)), "orkan_autotune")
+    return m.value, f.value
 
 
 def orkan_device_ptr(h) -> int:

@@ -415,3 +415,22 @@ def test_full_size_sampled(n, dtype):
             assert abs(ok.orkan_expect_pauli(h, s) - ref) <= TOL[dtype] * 10 * max(abs(ref), 1e-3), s
     finally:
         ok.orkan_free(h)
+
+
+# ------------------------------------------------------------------ autotuner
+def test_autotune_choice_is_valid_cached_and_exact():
+    m, f = ok.orkan_autotune(8, ok.ORKAN_DF64)
+    assert 3 <= m <= 5 and 1 <= f <= 16
+    assert ok.orkan_autotune(8, ok.ORKAN_DF64) == (m, f)        # cached for the process
+    rng = S.rng_for(6000)
+    n = 8
+    psi = S.haar_state_vector(rng, 1 << n)
+    ops = S.brickwork(n, 3, seed=6001)
+    ref, _ = D.run_circuit(np.outer(psi, psi.conj()), ops)
+    h = _handle(n, "df64", m, f, True)
+    try:
+        ok.orkan_init_state(h, ok.ORKAN_INIT_PURE, psi)
+        circuit.run_circuit(h, ops)
+        _assert_close(ok.orkan_to_dense(h), ref, "df64", "brickwork with autotuned settings")
+    finally:
+        ok.orkan_free(h)
