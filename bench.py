@@ -205,18 +205,19 @@ class Runner:
         self.bytes = ok.orkan_bytes(n, DTYPE_NAMES[dtype], m)
         self.step_idx = 0
         self.ops_per_step = 2 * len(wl["ops"]) + 1
+        # the sweep marshalled once into C-ABI op arrays (one orkan_run_circuit call per picture)
+        self.sch = circuit.marshal(wl["ops"], "schrodinger")
+        self.hei = circuit.marshal(list(reversed(wl["ops"])), "heisenberg")
 
     def step(self):
-        ok, c, wl = self.ok, self.circuit, self.wl
-        for op in wl["ops"]:
-            c.apply_op(self.rho, op, "schrodinger")
+        ok, wl = self.ok, self.wl
+        ok.orkan_run_circuit(self.rho, self.sch[0], 0)
         q = self.step_idx % self.n
         u = float(wl["us"][self.step_idx % len(wl["us"])])
         res = [ok.orkan_measure(self.rho, q, u)[1]]
         res += [ok.orkan_expect_pauli(self.rho, s) for s in wl["paulis"]]
         res.append(ok.orkan_trace(self.rho).real)
-        for op in reversed(wl["ops"]):
-            c.apply_op(self.O, op, "heisenberg")
+        ok.orkan_run_circuit(self.O, self.hei[0], 0)
         res.append(ok.orkan_expect(self.rho, self.O))
         self.step_idx += 1
         return res

@@ -163,6 +163,11 @@ int orkan_init_state(orkan_h h, int kind, const double *data);
  * Errors: EINVAL (bad character, nterms < 0), ENOMEM, ECUDA. */
 int orkan_init_observable(orkan_h h, int nterms, const char *paulis, const double *coeffs);
 
+/* Declare the handle's operator a state (Phi applies) or an observable (Phi*
+ * applies), e.g. after loading an observable with ORKAN_INIT_DENSE.  Pending
+ * ops are flushed in the old picture first. */
+int orkan_set_picture(orkan_h h, int picture);
+
 /* Raw tiled array copies (checkpoint / resume): host_src / host_dst hold
  * orkan_bytes(...) bytes in the handle's dtype and layout. */
 int orkan_load_tiled(orkan_h h, const void *host_src, int picture);
@@ -198,6 +203,33 @@ int orkan_measure(orkan_h h, int q, double u, int *outcome, double *prob);
 /* Pi_b H Pi_b without renormalisation (both pictures). */
 int orkan_project(orkan_h h, int q, int outcome);
 
+/* ------------------------------------------------------------------ whole circuits in one call */
+#define ORKAN_OP_UNITARY 0    /* mats: one 2^k x 2^k matrix */
+#define ORKAN_OP_KRAUS 1      /* mats: r matrices */
+#define ORKAN_OP_DEPOLARIZE 2 /* param = p */
+#define ORKAN_OP_DEPHASE 3    /* param = p */
+#define ORKAN_OP_AMPDAMP 4    /* param = gamma */
+#define ORKAN_OP_MEASURE 5    /* param = u (state handles only) */
+#define ORKAN_OP_PROJECT 6    /* outcome */
+
+typedef struct {
+  int kind;           /* ORKAN_OP_* */
+  int k;              /* qubits acted on (1 or 2; 1 for channels, measure, project) */
+  int qubits[2];
+  int r;              /* Kraus operators (ORKAN_OP_KRAUS) */
+  int outcome;        /* ORKAN_OP_PROJECT */
+  double param;       /* p, gamma or the uniform draw u */
+  const double *mats; /* complex128 matrices, row-major interleaved (UNITARY, KRAUS) */
+} orkan_op;
+
+/* Apply ops[0..count-1] in order with exactly the semantics of the single
+ * calls (orkan_apply_unitary, ..., orkan_measure, orkan_project); the j-th
+ * MEASURE op writes outcomes[j] and probs[j] (either may be NULL).  Stops at
+ * the first failing op and returns its status; *done (if not NULL) receives
+ * the number of ops applied.  One call per circuit keeps host overhead per op
+ * in the microseconds. */
+int orkan_run_circuit(orkan_h h, int count, const orkan_op *ops, int *outcomes, double *probs, int *done);
+
 /* ------------------------------------------------------------------ readouts (block; FP64) */
 
 /* tr H = sum_i H_ii (re, im). */
@@ -222,6 +254,21 @@ int orkan_get_elements(orkan_h h, int64_t count, const int64_t *rows, const int6
 /* Launch any pending fused ops / wait for the handle's stream. */
 int orkan_flush(orkan_h h);
 int orkan_sync(orkan_h h);
+
+/* ------------------------------------------------------------------ captured circuits
+ * Record the passes that the operations applied to h launch (a circuit of
+ * unitaries, channels and projections; fusion applies) into an executable
+ * CUDA graph, and replay it on the same handle: each replay applies the
+ * circuit again to the handle's current operator, without host planning or
+ * per-op launches.  Recording does not execute the circuit.  Between begin and
+ * end only operation calls are allowed; blocking calls (measure, readouts,
+ * init, sync) fail with EINVAL.  The handle needs a non-default stream (its
+ * own, or one set with orkan_set_stream).  A graph is bound to the handle's
+ * device memory and stays valid until orkan_graph_free. */
+int orkan_capture_begin(orkan_h h);
+int orkan_capture_end(orkan_h h, void **graph);
+int orkan_graph_launch(orkan_h h, void *graph);
+int orkan_graph_free(void *graph);
 
 /* ------------------------------------------------------------------ instrumentation */
 

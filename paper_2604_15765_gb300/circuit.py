@@ -35,10 +35,57 @@ def apply_op(h, op, picture: str = "schrodinger"):
     return None
 
 
-def run_circuit(h, ops, picture: str = "schrodinger"):
-    records = []
-    for op in ops:
-        rec = apply_op(h, op, picture)
-        if rec is not None:
-            records.append(rec)
-    return records
+def marshal(ops, picture: str = "schrodinger"):
+    """Op dicts -> (OrkanOp array, kept-alive matrices, number of MEASURE ops).
+    On an observable a measurement becomes the projection b = (u >= 0.5)."""
+    import numpy as np
+    arr = (ok.OrkanOp * len(ops))()
+    keep = []
+    nmeas = 0
+    for o, op in zip(arr, ops):
+        kind = op["kind"]
+        q = op["qubits"]
+        o.k = len(q)
+        o.qubits[0] = q[0]
+        o.qubits[1] = q[1] if len(q) > 1 else 0
+        if kind in ("unitary", "kraus"):
+            mats = np.ascontiguousarray(np.asarray(op["matrix"] if kind == "unitary" else op["mats"], np.complex128))
+            keep.append(mats)
+            o.kind = ok.ORKAN_OP_UNITARY if kind == "unitary" else ok.ORKAN_OP_KRAUS
+            o.r = 1 if kind == "unitary" else mats.shape[0]
+            o.mats = mats.view(np.float64).ctypes.data_as(ok._pd)
+        elif kind == "depolarize":
+            o.kind, o.param = ok.ORKAN_OP_DEPOLARIZE, op["p"]
+        elif kind == "dephase":
+            o.kind, o.param = ok.ORKAN_OP_DEPHASE, op["p"]
+        elif kind == "ampdamp":
+            o.kind, o.param = ok.ORKAN_OP_AMPDAMP, op["gamma"]
+        elif kind == "measure" and picture == "schrodinger":
+            o.kind, o.param = ok.ORKAN_OP_MEASURE, op["u"]
+            nmeas += 1
+        elif kind == "measure":
+            o.kind, o.outcome = ok.ORKAN_OP_PROJECT, 0 if op["u"] < 0.5 else 1
+        elif kind == "project":
+            o.kind, o.outcome = ok.ORKAN_OP_PROJECT, op["outcome"]
+        else:
+            raise ValueError(kind)
+    return arr, keep, nmeas
+
+
+def run_circuit(h, ops, picture: str = "schrodinger", native: bool = True):
+    """Apply an op list; with native=True the whole list goes through one
+    orkan_run_circuit call, else one binding call per op.  Returns the
+    measurement records [(outcome, prob)] in order."""
+    if not native:
+        records = []
+        for op in ops:
+            rec = apply_op(h, op, picture)
+            if rec is not None:
+                records.append(rec)
+        return records
+    arr, keep, nmeas = marshal(ops, picture)
+    outs, probs = ok.orkan_run_circuit(h, arr, nmeas)
+    del keep
+    if picture == "schrodinger":
+        return list(zip(outs, probs))
+    return [(0 if op["u"] < 0.5 else 1, None) for op in ops if op["kind"] == "measure"]

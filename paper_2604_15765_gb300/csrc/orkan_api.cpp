@@ -139,7 +139,36 @@ struct HostOp {
   int q[2] = {0, 0};           // ascending
   std::vector<double> R;       // single-qubit ops: full 4x4 PTM (for composition)
   std::vector<double> coef;    // kind-specific FP64 coefficients (2-qubit ops)
+  std::vector<long long> codes;  // monomial ops: permutation and phase codes
 };
+
+// A unitary is monomial with quarter-turn phases when every row holds exactly
+// one non-zero entry, equal to one of 1, i, -1, -i (tested exactly).  Then
+// V[i][p_i] = i^{q_i}; returns false otherwise.
+bool monomial(const Mat& V, int d, std::vector<long long>* p, std::vector<long long>* q) {
+  p->assign(d, 0);
+  q->assign(d, 0);
+  std::vector<int> used(d, 0);
+  for (int i = 0; i < d; ++i) {
+    int nz = 0;
+    for (int j = 0; j < d; ++j) {
+      const cd v = V[i * d + j];
+      if (v == cd(0.0, 0.0)) continue;
+      ++nz;
+      int code;
+      if (v == cd(1, 0)) code = 0;
+      else if (v == cd(0, 1)) code = 1;
+      else if (v == cd(-1, 0)) code = 2;
+      else if (v == cd(0, -1)) code = 3;
+      else return false;
+      (*p)[i] = j;
+      (*q)[i] = code;
+    }
+    if (nz != 1 || used[(*p)[i]]) return false;
+    used[(*p)[i]] = 1;
+  }
+  return true;
+}
 
 std::vector<double> mat4mul(const std::vector<double>& A, const std::vector<double>& B) {
   std::vector<double> C(16, 0.0);
@@ -201,6 +230,7 @@ struct orkan_ctx {
   size_t upload_cap = 0;     // which could synchronise the device under concurrent requests)
   int64_t n_passes = 0, n_ops = 0, n_launches = 0;
   bool timing = false;
+  bool capturing = false;
   std::vector<cudaEvent_t> ev_free;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
 };
@@ -311,13 +341,20 @@ int flush_pending(orkan_ctx* h) {
     }
     po.coef = slot;
     if (op.kind == OP_PTM2) d.has_ptm2 = 1;
+    if (op.nq == 1 && !op.codes.empty()) {
+      po.kind = OP_MONO1;
+      for (long long v : op.codes) std::memcpy(&d.coef[slot++], &v, 8);
+      continue;
+    }
     const std::vector<double> c = op.nq == 1 ? coef_1q(op.kind, op.R) : op.coef;
     for (double v : c) pack_coef(h, d, slot++, v);
+    for (long long v : op.codes) std::memcpy(&d.coef[slot++], &v, 8);
   }
   const int64_t nops = int64_t(h->pending.size());
   h->pending.clear();
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-  if (h->timing) {
+  const bool timed = h->timing && !h->capturing;
+  if (timed) {
     for (int i = 0; i < 2; ++i) {
       cudaEvent_t e;
       if (!h->ev_free.empty()) {
@@ -332,7 +369,7 @@ int flush_pending(orkan_ctx* h) {
   }
   int nlaunch = 0;
   ORKAN_CUDA(launch_pass(h->dtype, h->d_state, d, h->stream, &nlaunch));
-  if (h->timing) {
+  if (timed) {
     ORKAN_CUDA(cudaEventRecord(ev.second, h->stream));
     h->ev_used.push_back(ev);
   }
@@ -348,6 +385,7 @@ int enqueue(orkan_ctx* h, HostOp op) {
     HostOp& last = h->pending.back();
     if (last.nq == 1 && last.q[0] == op.q[0]) {
       last.R = mat4mul(op.R, last.R);
+      last.codes.clear();
       if (!(last.kind == op.kind && (op.kind == OP_PTM1_U || op.kind == OP_PTM1_AD))) {
         last.kind = is_unitary_pattern(last.R) ? OP_PTM1_U : (is_ad_pattern(last.R) ? OP_PTM1_AD : OP_PTM1);
       }
@@ -368,6 +406,12 @@ int check_handle(orkan_h h) {
   if (!h) return fail(ORKAN_EINVAL, "null handle");
   return ORKAN_OK;
 }
+// Calls that wait for the device or read results cannot be recorded into a graph.
+int check_blocking(orkan_h h) {
+  if (int st = check_handle(h)) return st;
+  if (h->capturing) return fail(ORKAN_EINVAL, "not allowed while capturing a graph (blocking call)");
+  return ORKAN_OK;
+}
 
 int check_qubits(const orkan_ctx* h, int k, const int* qubits) {
   if (k < 1 || k > 2 || !qubits) return fail(ORKAN_EINVAL, "k must be 1 or 2 with a qubit list");
@@ -386,6 +430,13 @@ int make_op(orkan_ctx* h, int k, const int* qubits, const std::vector<Mat>& krau
   if (k == 1) {
     op.q[0] = qubits[0];
     op.R = ptm(1, kraus, adj);
+    std::vector<long long> pp, qq;
+    if (unitary && monomial(adj ? dagger(kraus[0], 2) : kraus[0], 2, &pp, &qq)) {
+      op.kind = OP_PTM1_U;   // composes as a unitary PTM if a neighbour merges into it
+      op.codes = {pp[0], pp[1], qq[0], qq[1]};
+      *out = std::move(op);
+      return ORKAN_OK;
+    }
     if (unitary) {
       // a unitary conjugation fixes the identity and is trace preserving
       op.R[0] = 1.0;
@@ -406,11 +457,16 @@ int make_op(orkan_ctx* h, int k, const int* qubits, const std::vector<Mat>& krau
     if (kraus.size() == 1) {
       // direct form h -> V h V^dagger (Eq. 2 with r = 1)
       const Mat V = adj ? dagger(kraus[0], 4) : kraus[0];
-      op.kind = OP_U2;
+      std::vector<long long> pp, qq;
+      op.kind = (unitary && monomial(V, 4, &pp, &qq)) ? OP_MONO2 : OP_U2;
       op.coef.resize(32);
       for (int i = 0; i < 16; ++i) {
         op.coef[2 * i] = V[i].real();
         op.coef[2 * i + 1] = V[i].imag();
+      }
+      if (op.kind == OP_MONO2) {
+        op.codes = pp;
+        op.codes.insert(op.codes.end(), qq.begin(), qq.end());
       }
     } else {
       const std::vector<double> R = ptm(2, kraus, adj);
@@ -628,7 +684,7 @@ int orkan_free(orkan_h h) {
 }
 
 int orkan_set_stream(orkan_h h, void* cuda_stream) {
-  if (int st = check_handle(h)) return st;
+  if (int st = check_blocking(h)) return st;
   if (int st = flush_pending(h)) return st;
   if (h->own_stream && h->stream) {
     ORKAN_CUDA(cudaStreamSynchronize(h->stream));
@@ -660,7 +716,7 @@ int orkan_get_info(orkan_h h, int* n, int* dtype, int* tile_log2, int* picture) 
 void* orkan_device_ptr(orkan_h h) { return h ? h->d_state : nullptr; }
 
 int orkan_init_state(orkan_h h, int kind, const double* data) {
-  if (int st = check_handle(h)) return st;
+  if (int st = check_blocking(h)) return st;
   h->pending.clear();
   h->picture = ORKAN_STATE;
   switch (kind) {
@@ -692,8 +748,16 @@ int orkan_init_state(orkan_h h, int kind, const double* data) {
   return fail(ORKAN_EINVAL, "unknown init kind");
 }
 
-int orkan_init_observable(orkan_h h, int nterms, const char* paulis, const double* coeffs) {
+int orkan_set_picture(orkan_h h, int picture) {
   if (int st = check_handle(h)) return st;
+  if (picture != ORKAN_STATE && picture != ORKAN_OBSERVABLE) return fail(ORKAN_EINVAL, "bad picture");
+  if (int st = flush_pending(h)) return st;
+  h->picture = picture;
+  return ORKAN_OK;
+}
+
+int orkan_init_observable(orkan_h h, int nterms, const char* paulis, const double* coeffs) {
+  if (int st = check_blocking(h)) return st;
   if (nterms < 0 || (nterms > 0 && (!paulis || !coeffs))) return fail(ORKAN_EINVAL, "bad Pauli sum");
   const int n = h->g.n;
   struct Term {
@@ -741,7 +805,7 @@ int orkan_init_observable(orkan_h h, int nterms, const char* paulis, const doubl
 }
 
 int orkan_load_tiled(orkan_h h, const void* host_src, int picture) {
-  if (int st = check_handle(h)) return st;
+  if (int st = check_blocking(h)) return st;
   if (!host_src || (picture != ORKAN_STATE && picture != ORKAN_OBSERVABLE)) return fail(ORKAN_EINVAL, "bad args");
   h->pending.clear();
   h->picture = picture;
@@ -751,7 +815,7 @@ int orkan_load_tiled(orkan_h h, const void* host_src, int picture) {
 }
 
 int orkan_store_tiled(orkan_h h, void* host_dst) {
-  if (int st = check_handle(h)) return st;
+  if (int st = check_blocking(h)) return st;
   if (!host_dst) return fail(ORKAN_EINVAL, "null destination");
   if (int st = flush_pending(h)) return st;
   ORKAN_CUDA(cudaMemcpyAsync(host_dst, h->d_state, h->bytes, cudaMemcpyDeviceToHost, h->stream));
@@ -813,7 +877,7 @@ int orkan_amplitude_damp(orkan_h h, int q, double gamma) {
 }
 
 int orkan_measure(orkan_h h, int q, double u, int* outcome, double* prob) {
-  if (int st = check_handle(h)) return st;
+  if (int st = check_blocking(h)) return st;
   if (h->picture != ORKAN_STATE) return fail(ORKAN_EPICTURE, "measure needs a state handle (use orkan_project)");
   if (int st = check_qubits(h, 1, &q)) return st;
   if (!(u >= 0.0 && u < 1.0)) return fail(ORKAN_EINVAL, "u must be in [0, 1)");
@@ -843,8 +907,39 @@ int orkan_project(orkan_h h, int q, int outcome) {
   return enqueue(h, make_ad_op(q, R));
 }
 
-int orkan_trace(orkan_h h, double* re, double* im) {
+int orkan_run_circuit(orkan_h h, int count, const orkan_op* ops, int* outcomes, double* probs, int* done) {
   if (int st = check_handle(h)) return st;
+  if (count < 0 || (count > 0 && !ops)) return fail(ORKAN_EINVAL, "bad op list");
+  int nmeas = 0, i = 0, st = ORKAN_OK;
+  for (; i < count && st == ORKAN_OK; ++i) {
+    const orkan_op& o = ops[i];
+    switch (o.kind) {
+      case ORKAN_OP_UNITARY: st = orkan_apply_unitary(h, o.k, o.qubits, o.mats); break;
+      case ORKAN_OP_KRAUS: st = orkan_apply_kraus(h, o.k, o.qubits, o.r, o.mats); break;
+      case ORKAN_OP_DEPOLARIZE: st = orkan_depolarize(h, o.qubits[0], o.param); break;
+      case ORKAN_OP_DEPHASE: st = orkan_dephase(h, o.qubits[0], o.param); break;
+      case ORKAN_OP_AMPDAMP: st = orkan_amplitude_damp(h, o.qubits[0], o.param); break;
+      case ORKAN_OP_MEASURE: {
+        int b = 0;
+        double pr = 0.0;
+        st = orkan_measure(h, o.qubits[0], o.param, &b, &pr);
+        if (st == ORKAN_OK) {
+          if (outcomes) outcomes[nmeas] = b;
+          if (probs) probs[nmeas] = pr;
+          ++nmeas;
+        }
+        break;
+      }
+      case ORKAN_OP_PROJECT: st = orkan_project(h, o.qubits[0], o.outcome); break;
+      default: st = fail(ORKAN_EINVAL, "unknown op kind");
+    }
+  }
+  if (done) *done = st == ORKAN_OK ? i : i - 1;
+  return st;
+}
+
+int orkan_trace(orkan_h h, double* re, double* im) {
+  if (int st = check_blocking(h)) return st;
   double r[4];
   if (int st = reduce_diag(h, -1, r)) return st;
   if (re) *re = r[0];
@@ -853,7 +948,7 @@ int orkan_trace(orkan_h h, double* re, double* im) {
 }
 
 int orkan_expect_pauli(orkan_h h, const char* pauli, double* out) {
-  if (int st = check_handle(h)) return st;
+  if (int st = check_blocking(h)) return st;
   if (!pauli || !out) return fail(ORKAN_EINVAL, "null argument");
   uint64_t x = 0, z = 0, y = 0;
   int ny = 0;
@@ -884,8 +979,8 @@ int orkan_expect_pauli(orkan_h h, const char* pauli, double* out) {
 }
 
 int orkan_expect(orkan_h rho, orkan_h O, double* out) {
-  if (int st = check_handle(rho)) return st;
-  if (int st = check_handle(O)) return st;
+  if (int st = check_blocking(rho)) return st;
+  if (int st = check_blocking(O)) return st;
   if (!out) return fail(ORKAN_EINVAL, "null output");
   if (rho->g.n != O->g.n || rho->g.m != O->g.m || rho->dtype != O->dtype)
     return fail(ORKAN_EINVAL, "operands differ in n, tile size or dtype");
@@ -902,7 +997,7 @@ int orkan_expect(orkan_h rho, orkan_h O, double* out) {
 }
 
 int orkan_to_dense(orkan_h h, double* out) {
-  if (int st = check_handle(h)) return st;
+  if (int st = check_blocking(h)) return st;
   if (!out) return fail(ORKAN_EINVAL, "null output");
   if (int st = flush_pending(h)) return st;
   const size_t bytes = size_t(h->g.N) * size_t(h->g.N) * 16;
@@ -921,7 +1016,7 @@ int orkan_to_dense(orkan_h h, double* out) {
 }
 
 int orkan_get_elements(orkan_h h, int64_t count, const int64_t* rows, const int64_t* cols, double* out) {
-  if (int st = check_handle(h)) return st;
+  if (int st = check_blocking(h)) return st;
   if (count < 0 || (count > 0 && (!rows || !cols || !out))) return fail(ORKAN_EINVAL, "bad element list");
   if (count == 0) return flush_pending(h);
   for (int64_t t = 0; t < count; ++t)
@@ -953,9 +1048,52 @@ int orkan_flush(orkan_h h) {
 }
 
 int orkan_sync(orkan_h h) {
-  if (int st = check_handle(h)) return st;
+  if (int st = check_blocking(h)) return st;
   if (int st = flush_pending(h)) return st;
   ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+  return ORKAN_OK;
+}
+
+int orkan_capture_begin(orkan_h h) {
+  if (int st = check_blocking(h)) return st;
+  if (!h->stream) return fail(ORKAN_EINVAL, "graph capture needs a non-default stream (see orkan_set_stream)");
+  if (int st = flush_pending(h)) return st;
+  ORKAN_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  h->capturing = true;
+  return ORKAN_OK;
+}
+
+int orkan_capture_end(orkan_h h, void** graph) {
+  if (int st = check_handle(h)) return st;
+  if (!h->capturing || !graph) return fail(ORKAN_EINVAL, "no capture in progress or null output");
+  const int fst = flush_pending(h);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  h->capturing = false;
+  if (fst != ORKAN_OK) {
+    if (g) cudaGraphDestroy(g);
+    return fst;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  *graph = ex;
+  return ORKAN_OK;
+}
+
+int orkan_graph_launch(orkan_h h, void* graph) {
+  if (int st = check_blocking(h)) return st;
+  if (!graph) return fail(ORKAN_EINVAL, "null graph");
+  if (int st = flush_pending(h)) return st;
+  ORKAN_CUDA(cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph), h->stream));
+  h->n_launches += 1;
+  return ORKAN_OK;
+}
+
+int orkan_graph_free(void* graph) {
+  if (graph) ORKAN_CUDA(cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(graph)));
   return ORKAN_OK;
 }
 
@@ -968,14 +1106,14 @@ int orkan_stats(orkan_h h, int64_t* passes, int64_t* ops, int64_t* launches) {
 }
 
 int orkan_set_timing(orkan_h h, int enable) {
-  if (int st = check_handle(h)) return st;
+  if (int st = check_blocking(h)) return st;
   if (int st = flush_pending(h)) return st;
   h->timing = enable != 0;
   return ORKAN_OK;
 }
 
 int orkan_pass_time(orkan_h h, double* ms, int64_t* count) {
-  if (int st = check_handle(h)) return st;
+  if (int st = check_blocking(h)) return st;
   if (int st = flush_pending(h)) return st;
   ORKAN_CUDA(cudaStreamSynchronize(h->stream));
   double total = 0.0;

@@ -20,7 +20,13 @@ enum Dtype : int { DT_C128 = 0, DT_C64 = 1, DT_DF64 = 2 };
 //             (depolarising, dephasing, amplitude damping, projectors, Rz)
 //   U2      : two-qubit unitary, direct form V h V^dagger (Eq. 2 with r = 1)
 //   PTM2    : generic two-qubit map, Pauli transfer matrix R/4 (16x16 real)
-enum OpKind : int { OP_PTM1 = 0, OP_PTM1_U = 1, OP_PTM1_AD = 2, OP_U2 = 3, OP_PTM2 = 4 };
+//   MONO1 / MONO2 : unitaries whose every row has one non-zero entry, a unit
+//             phase i^q (X, Y, Z, S, CNOT, CZ, SWAP, iSWAP, ...): conjugation is
+//             a permutation of the block with quarter-turn phase factors,
+//             without floating-point arithmetic (Sec. II-B native gates).
+//             Coefficients: MONO1 = (p0, p1, q0, q1); MONO2 = the dense V (32
+//             slots, for the block form) then (p0..p3, q0..q3).
+enum OpKind : int { OP_PTM1 = 0, OP_PTM1_U = 1, OP_PTM1_AD = 2, OP_U2 = 3, OP_PTM2 = 4, OP_MONO1 = 5, OP_MONO2 = 6 };
 
 constexpr int kMaxOps = 16;     // ops fused into one pass
 constexpr int kMaxCoef = 640;   // 8-byte coefficient slots per pass
@@ -33,6 +39,8 @@ inline int coef_slots(int kind) {
     case OP_PTM1_AD: return 6;
     case OP_U2: return 32;      // 16 complex entries, re/im interleaved
     case OP_PTM2: return 256;
+    case OP_MONO1: return 4;
+    case OP_MONO2: return 40;
   }
   return 0;
 }

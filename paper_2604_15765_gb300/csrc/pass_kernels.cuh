@@ -157,6 +157,37 @@ __device__ __forceinline__ void body_ptm1_ad(Cx<P>& a, Cx<P>& b, Cx<P>& c, Cx<P>
   b.re = br; b.im = bi; c.re = cr; c.im = ci;
 }
 
+// Integer codes of monomial ops are stored as raw 64-bit integers in their slots.
+__device__ __forceinline__ int icoef(const double* cf, int i) {
+  return int(reinterpret_cast<const long long*>(cf)[i]);
+}
+
+// z * i^k for k = 0..3: exact (swaps and sign flips of the parts).
+template <class P>
+__device__ __forceinline__ Cx<P> rot_i(const Cx<P>& z, int k) {
+  switch (k & 3) {
+    case 0: return z;
+    case 1: return Cx<P>{P::neg(z.im), z.re};
+    case 2: return Cx<P>{P::neg(z.re), P::neg(z.im)};
+    default: return Cx<P>{z.im, P::neg(z.re)};
+  }
+}
+
+// Monomial single-qubit unitary V[i][p_i] = i^{q_i}: (V h V^dagger)[i][j] =
+// i^{q_i - q_j} h[p_i][p_j].
+template <class P>
+__device__ __forceinline__ void body_mono1(Cx<P>& a, Cx<P>& b, Cx<P>& c, Cx<P>& d, const double* cf) {
+  const int p0 = icoef(cf, 0), p1 = icoef(cf, 1), q0 = icoef(cf, 2), q1 = icoef(cf, 3);
+  const Cx<P> h00 = a, h01 = b, h10 = c, h11 = d;
+  auto pick = [&](int r, int s) -> Cx<P> {
+    return r ? (s ? h11 : h10) : (s ? h01 : h00);
+  };
+  a = rot_i<P>(pick(p0, p0), q0 - q0);
+  b = rot_i<P>(pick(p0, p1), q0 - q1);
+  c = rot_i<P>(pick(p1, p0), q1 - q0);
+  d = rot_i<P>(pick(p1, p1), q1 - q1);
+}
+
 // Two-qubit unitary, h <- V h V^dagger, in registers: first every row of h is
 // replaced by h[k,:] V^dagger, then every column by V (.)[:, j].
 template <class P>
@@ -306,6 +337,18 @@ __device__ __forceinline__ void matvec4(const Cx<P> (&in)[4], Cx<P> (&out)[4], c
   }
 }
 
+// out[i] = i^{q_i} in[p_i] (V) or out[j] = i^{-q_j} in[p_j] (conj(V) applied as
+// h V^dagger on a row): the monomial form of matvec4, no arithmetic.
+template <class P, bool CONJ>
+__device__ __forceinline__ void matvec4_mono(const Cx<P> (&in)[4], Cx<P> (&out)[4], const double* cf) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int p = icoef(cf, i), q = icoef(cf, 4 + i);
+    const Cx<P> x = p == 0 ? in[0] : (p == 1 ? in[1] : (p == 2 ? in[2] : in[3]));
+    out[i] = rot_i<P>(x, CONJ ? -q : q);
+  }
+}
+
 // ------------------------------------------------------------------ op drivers
 template <class P, class G, int NT, int rows_log2g, int cols_log2g>
 __device__ __forceinline__ void apply_1q(typename P::Elem* sm, const G& gm, const PassOp& op, const double* coef) {
@@ -325,6 +368,7 @@ __device__ __forceinline__ void apply_1q(typename P::Elem* sm, const G& gm, cons
     Cx<P> a = ld<P>(sm, i00), bb = ld<P>(sm, i01), c = ld<P>(sm, i10), d = ld<P>(sm, i11);
     if (op.kind == OP_PTM1_U) body_ptm1_u<P>(a, bb, c, d, cf);
     else if (op.kind == OP_PTM1_AD) body_ptm1_ad<P>(a, bb, c, d, cf);
+    else if (op.kind == OP_MONO1) body_mono1<P>(a, bb, c, d, cf);
     else body_ptm1<P>(a, bb, c, d, cf);
     st<P>(sm, i00, a);
     st<P>(sm, i01, bb);
@@ -359,7 +403,8 @@ __device__ __forceinline__ void apply_u2_sep(typename P::Elem* sm, const G& gm, 
       Cx<P> in[4], out[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) in[a] = ld<P>(sm, ix[a]);
-      matvec4<P, true>(in, out, cf);
+      if (op.kind == OP_MONO2) matvec4_mono<P, true>(in, out, cf + 32);
+      else matvec4<P, true>(in, out, cf);
 #pragma unroll
       for (int a = 0; a < 4; ++a) st<P>(sm, ix[a], out[a]);
     }
@@ -382,7 +427,8 @@ __device__ __forceinline__ void apply_u2_sep(typename P::Elem* sm, const G& gm, 
       Cx<P> in[4], out[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) in[a] = ld<P>(sm, ix[a]);
-      matvec4<P, false>(in, out, cf);
+      if (op.kind == OP_MONO2) matvec4_mono<P, false>(in, out, cf + 32);
+      else matvec4<P, false>(in, out, cf);
 #pragma unroll
       for (int a = 0; a < 4; ++a) st<P>(sm, ix[a], out[a]);
     }
@@ -598,7 +644,8 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
     for (int o = 0; o < d.nops; ++o) {
       const PassOp& op = d.ops[o];
       if (op.nq == 1) apply_1q<P, G, kMainThreads, rows_log2g, cols_log2g>(sm, gm, op, d.coef);
-      else if (!P2 || op.kind == OP_U2) apply_u2_sep<P, G, kMainThreads, rows_log2g, cols_log2g>(sm, gm, op, d.coef);
+      else if (!P2 || op.kind == OP_U2 || op.kind == OP_MONO2)
+        apply_u2_sep<P, G, kMainThreads, rows_log2g, cols_log2g>(sm, gm, op, d.coef);
       else if constexpr (P2) apply_ptm2<P, G, kMainThreads, rows_log2g, cols_log2g>(sm, gm, op, d.coef);
       __syncthreads();
     }
@@ -698,6 +745,7 @@ __device__ __forceinline__ void diag_apply(typename P::Elem* sm, const DMap& mp,
       Cx<P> c = dread<P>(sm, mp, rb | bit, cb), d = dread<P>(sm, mp, rb | bit, cb | bit);
       if (op.kind == OP_PTM1_U) body_ptm1_u<P>(a, bb, c, d, cf);
       else if (op.kind == OP_PTM1_AD) body_ptm1_ad<P>(a, bb, c, d, cf);
+      else if (op.kind == OP_MONO1) body_mono1<P>(a, bb, c, d, cf);
       else body_ptm1<P>(a, bb, c, d, cf);
       dwrite<P>(sm, mp, rb, cb, a);
       dwrite<P>(sm, mp, rb, cb | bit, bb);
@@ -717,7 +765,7 @@ __device__ __forceinline__ void diag_apply(typename P::Elem* sm, const DMap& mp,
       for (int ra = 0; ra < 4; ++ra)
 #pragma unroll
         for (int ca = 0; ca < 4; ++ca) h[4 * ra + ca] = dread<P>(sm, mp, rows[ra], cols[ca]);
-      if (op.kind == OP_U2) body_u2<P>(h, cf);
+      if (op.kind == OP_U2 || op.kind == OP_MONO2) body_u2<P>(h, cf);
       else body_ptm2<P>(h, cf);
 #pragma unroll
       for (int ra = 0; ra < 4; ++ra)

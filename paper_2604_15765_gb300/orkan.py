@@ -34,6 +34,16 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 _h = C.c_void_p
+
+
+class OrkanOp(C.Structure):
+    """orkan_op of include/orkan.h."""
+    _fields_ = [("kind", C.c_int), ("k", C.c_int), ("qubits", C.c_int * 2), ("r", C.c_int), ("outcome", C.c_int),
+                ("param", C.c_double), ("mats", C.POINTER(C.c_double))]
+
+
+ORKAN_OP_UNITARY, ORKAN_OP_KRAUS, ORKAN_OP_DEPOLARIZE, ORKAN_OP_DEPHASE = 0, 1, 2, 3
+ORKAN_OP_AMPDAMP, ORKAN_OP_MEASURE, ORKAN_OP_PROJECT = 4, 5, 6
 _i64 = C.c_int64
 _pd = C.POINTER(C.c_double)
 _pi = C.POINTER(C.c_int)
@@ -56,6 +66,7 @@ _SIGS = {
     "orkan_device_ptr": (C.c_void_p, [_h]),
     "orkan_init_state": (C.c_int, [_h, C.c_int, _pd]),
     "orkan_init_observable": (C.c_int, [_h, C.c_int, C.c_char_p, _pd]),
+    "orkan_set_picture": (C.c_int, [_h, C.c_int]),
     "orkan_load_tiled": (C.c_int, [_h, C.c_void_p, C.c_int]),
     "orkan_store_tiled": (C.c_int, [_h, C.c_void_p]),
     "orkan_apply_unitary": (C.c_int, [_h, C.c_int, _pi, _pd]),
@@ -65,6 +76,7 @@ _SIGS = {
     "orkan_amplitude_damp": (C.c_int, [_h, C.c_int, C.c_double]),
     "orkan_measure": (C.c_int, [_h, C.c_int, C.c_double, _pi, _pd]),
     "orkan_project": (C.c_int, [_h, C.c_int, C.c_int]),
+    "orkan_run_circuit": (C.c_int, [_h, C.c_int, C.POINTER(OrkanOp), _pi, _pd, _pi]),
     "orkan_trace": (C.c_int, [_h, _pd, _pd]),
     "orkan_expect_pauli": (C.c_int, [_h, C.c_char_p, _pd]),
     "orkan_expect": (C.c_int, [_h, _h, _pd]),
@@ -73,6 +85,10 @@ _SIGS = {
     "orkan_flush": (C.c_int, [_h]),
     "orkan_sync": (C.c_int, [_h]),
     "orkan_stats": (C.c_int, [_h, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)]),
+    "orkan_capture_begin": (C.c_int, [_h]),
+    "orkan_capture_end": (C.c_int, [_h, C.POINTER(C.c_void_p)]),
+    "orkan_graph_launch": (C.c_int, [_h, C.c_void_p]),
+    "orkan_graph_free": (C.c_int, [C.c_void_p]),
     "orkan_set_timing": (C.c_int, [_h, C.c_int]),
     "orkan_pass_time": (C.c_int, [_h, _pd, C.POINTER(_i64)]),
     "orkan_expect_paulis_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_char_p, _pd,
@@ -192,6 +208,10 @@ def orkan_init_observable(h, paulis, coeffs):
     _check(_lib.orkan_init_observable(h, len(paulis), s, _dptr(c)), "orkan_init_observable")
 
 
+def orkan_set_picture(h, picture: int):
+    _check(_lib.orkan_set_picture(h, picture), "orkan_set_picture")
+
+
 def orkan_load_tiled(h, host_buf: np.ndarray, picture: int = ORKAN_STATE):
     buf = np.ascontiguousarray(host_buf)
     _check(_lib.orkan_load_tiled(h, buf.ctypes.data_as(C.c_void_p), picture), "orkan_load_tiled")
@@ -239,6 +259,15 @@ def orkan_project(h, q: int, outcome: int):
     _check(_lib.orkan_project(h, q, outcome), "orkan_project")
 
 
+def orkan_run_circuit(h, ops_array, n_measure: int):
+    """Apply a prepared OrkanOp array in one call; returns (outcomes, probs)."""
+    outs = (C.c_int * max(n_measure, 1))()
+    probs = (C.c_double * max(n_measure, 1))()
+    done = C.c_int()
+    _check(_lib.orkan_run_circuit(h, len(ops_array), ops_array, outs, probs, C.byref(done)), "orkan_run_circuit")
+    return list(outs)[:n_measure], list(probs)[:n_measure]
+
+
 # ------------------------------------------------------------------ readouts
 def orkan_trace(h):
     re, im = C.c_double(), C.c_double()
@@ -282,6 +311,24 @@ def orkan_flush(h):
 
 def orkan_sync(h):
     _check(_lib.orkan_sync(h), "orkan_sync")
+
+
+def orkan_capture_begin(h):
+    _check(_lib.orkan_capture_begin(h), "orkan_capture_begin")
+
+
+def orkan_capture_end(h):
+    g = C.c_void_p()
+    _check(_lib.orkan_capture_end(h, C.byref(g)), "orkan_capture_end")
+    return g
+
+
+def orkan_graph_launch(h, graph):
+    _check(_lib.orkan_graph_launch(h, graph), "orkan_graph_launch")
+
+
+def orkan_graph_free(graph):
+    _check(_lib.orkan_graph_free(graph), "orkan_graph_free")
 
 
 def orkan_stats(h):

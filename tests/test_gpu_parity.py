@@ -434,3 +434,104 @@ def test_autotune_choice_is_valid_cached_and_exact():
         _assert_close(ok.orkan_to_dense(h), ref, "df64", "brickwork with autotuned settings")
     finally:
         ok.orkan_free(h)
+
+
+# ------------------------------------------------------------------ native (monomial) gates
+_S = np.diag([1, 1j]).astype(np.complex128)
+_CNOT = np.eye(4, dtype=np.complex128)[[0, 3, 2, 1]]      # control = index bit 0
+_CZ = np.diag([1, 1, 1, -1]).astype(np.complex128)
+_SWAP = np.eye(4, dtype=np.complex128)[[0, 2, 1, 3]]
+_ISWAP = np.array([[1, 0, 0, 0], [0, 0, 1j, 0], [0, 1j, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "df64", "c64"])
+@pytest.mark.parametrize("picture", ["schrodinger", "heisenberg"])
+def test_monomial_gates(dtype, picture):
+    """X, Y, Z, S, S^dagger, CNOT, CZ, SWAP, iSWAP are permutations with
+    quarter-turn phases (Sec. II-B native gates): applied without arithmetic,
+    so native FP64 reproduces the oracle bit for bit."""
+    n, m = 9, 3
+    rng = S.rng_for(6500)
+    H0 = S.random_hermitian(rng, 1 << n)
+    gates1 = [D.X, D.Y, D.Z, _S, _S.conj().T]
+    gates2 = [_CNOT, _CZ, _SWAP, _ISWAP]
+    h = _handle(n, dtype, m, fusion=4, compose=False)
+    try:
+        for q in (0, 2, 3, 8):
+            for U in gates1:
+                ops = [S.op_unitary(U, [q])]
+                _check_ops(h, H0, ops, dtype, picture, exact=(dtype == "c128"))
+        for pair in ((0, 1), (1, 0), (2, 7), (8, 3), (5, 6)):
+            for U in gates2:
+                _check_ops(h, H0, [S.op_unitary(U, list(pair))], dtype, picture, exact=(dtype == "c128"))
+        # fused runs mixing monomial and dense ops
+        mix = [S.op_unitary(D.X, [4]), S.op_unitary(_CNOT, [4, 7]), S.op_unitary(S.haar_unitary(rng, 2), [4]),
+               S.op_unitary(_ISWAP, [7, 8]), S.op_depolarize(8, 0.1), S.op_unitary(D.Y, [1])]
+        _check_ops(h, H0, mix, dtype, picture, exact=False)
+    finally:
+        ok.orkan_free(h)
+
+
+def _check_ops(h, H0, ops, dtype, picture, exact):
+    ok.orkan_init_state(h, ok.ORKAN_INIT_DENSE, H0)
+    if picture == "heisenberg":
+        ok.orkan_set_picture(h, ok.ORKAN_OBSERVABLE)
+    circuit.run_circuit(h, ops, picture)
+    ref, _ = D.run_circuit(H0, ops, picture)
+    got = ok.orkan_to_dense(h)
+    if exact:
+        assert np.array_equal(got, ref), [o["qubits"] for o in ops]
+    else:
+        _assert_close(got, ref, dtype, str([o["qubits"] for o in ops]))
+
+
+# ------------------------------------------------------------------ captured circuits
+@pytest.mark.parametrize("dtype", ["c128", "df64", "c64"])
+def test_graph_capture_replay(dtype):
+    n = 9
+    rng = S.rng_for(6600)
+    rho0 = S.ginibre_state(rng, 1 << n)
+    ops = S.random_mixed_circuit(rng, n, 40, with_measure=False)
+    h1, h2 = _handle(n, dtype, 5), _handle(n, dtype, 5)
+    try:
+        ok.orkan_init_state(h1, ok.ORKAN_INIT_DENSE, rho0)
+        ok.orkan_init_state(h2, ok.ORKAN_INIT_DENSE, rho0)
+        ok.orkan_sync(h1)
+        ok.orkan_capture_begin(h1)
+        circuit.run_circuit(h1, ops)
+        with pytest.raises(ok.OrkanError):
+            ok.orkan_trace(h1)                     # blocking calls are refused while recording
+        g = ok.orkan_capture_end(h1)
+        assert np.array_equal(ok.orkan_to_dense(h1), ok.orkan_to_dense(h2))   # recording runs nothing
+        ok.orkan_graph_launch(h1, g)
+        ok.orkan_graph_launch(h1, g)
+        circuit.run_circuit(h2, ops)
+        circuit.run_circuit(h2, ops)
+        assert np.array_equal(ok.orkan_to_dense(h1), ok.orkan_to_dense(h2))
+        ref, _ = D.run_circuit(rho0, ops + ops)
+        _assert_close(ok.orkan_to_dense(h1), ref, dtype, "replayed circuit")
+        ok.orkan_graph_free(g)
+    finally:
+        ok.orkan_free(h1)
+        ok.orkan_free(h2)
+
+
+# ------------------------------------------------------------------ one-call circuits
+@pytest.mark.parametrize("dtype", ["c128", "df64", "c64"])
+def test_native_circuit_runner_matches_per_op_calls(dtype):
+    w = S.config0(n=7, depth=80)
+    for picture in ("schrodinger", "heisenberg"):
+        hs = [_handle(7, dtype, 5), _handle(7, dtype, 5)]
+        try:
+            for h in hs:
+                ok.orkan_init_state(h, ok.ORKAN_INIT_DENSE, w["rho"])
+                if picture == "heisenberg":
+                    ok.orkan_set_picture(h, ok.ORKAN_OBSERVABLE)
+            ops = w["ops"] if picture == "schrodinger" else [o for o in w["ops"] if o["kind"] != "measure"]
+            r1 = circuit.run_circuit(hs[0], ops, picture, native=True)
+            r2 = circuit.run_circuit(hs[1], ops, picture, native=False)
+            assert r1 == r2
+            assert np.array_equal(ok.orkan_to_dense(hs[0]), ok.orkan_to_dense(hs[1]))
+        finally:
+            for h in hs:
+                ok.orkan_free(h)
