@@ -169,6 +169,12 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# ALU peaks of GB300 (152 SMs at the 2070 MHz maximum clock; per-SM rates measured by the pipe probe,
+# profiles/gb300_pipe_rates.md): FP32 pipe 128 lane-ops per clock per SM, FP64 pipe 2 per clock per SM.
+ALU_PEAK_TOPS = {"df64": 152 * 128 * 2.07e9 / 1e12, "c64": 152 * 128 * 2.07e9 / 1e12,
+                 "c128": 152 * 2.0 * 2.07e9 / 1e12}
+
+
 def traffic_record(dtype: str):
     """DRAM bytes per pass-kernel launch from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
@@ -231,7 +237,11 @@ class Runner:
 
     def pass_time(self):
         ms, cnt = 0.0, 0
+        self.work = [0.0, 0.0]
         for h in (self.rho, self.O):
+            w = self.ok.orkan_pass_work(h)
+            self.work[0] += w[0]
+            self.work[1] += w[1]
             a, b = self.ok.orkan_pass_time(h)
             ms += a
             cnt += b
@@ -624,10 +634,24 @@ def main(argv=None):
     hbm_peak, peak_kind = peaks()
     avg_pass_ms = pass_ms / max(pass_cnt, 1)
     achieved = 2.0 * runner.bytes / (avg_pass_ms * 1e-3) / 1e9
+    alu_ops = runner.work[0]
+    alu_tops = alu_ops / (pass_ms * 1e-3) / 1e12 if pass_ms > 0 else 0.0
+    alu_peak = ALU_PEAK_TOPS[args.dtype]
     trec = traffic_record(args.dtype)
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": (trec or {}).get("bytes_per_launch"),
-                "kernel": "pass_kernel (fused tile-group conjugation)", "peak_kind": f"{peak_kind} hbm_gbs",
+    hbm = {"achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+           "peak_kind": f"{peak_kind} hbm_gbs"}
+    alu = {"achieved": round(alu_tops, 2), "peak": round(alu_peak, 2),
+           "unit": "Tops/s (" + ("FP64-pipe ops" if args.dtype == "c128" else "FP32-pipe lane ops") + ")",
+           "frac": round(alu_tops / alu_peak, 4),
+           "peak_kind": "derived: 152 SMs x pipe rate per clock (measured probe) x 2.07 GHz",
+           "algorithmic_ops_per_launch": round(alu_ops / max(pass_cnt, 1))}
+    # the binding roofline is the one the pass kernel runs closer to
+    bound = "alu" if alu["frac"] >= hbm["frac"] else "hbm"
+    main = alu if bound == "alu" else hbm
+    roofline = {"bound": bound, "achieved": main["achieved"], "peak": main["peak"], "unit": main["unit"],
+                "frac": main["frac"], "traffic": (trec or {}).get("bytes_per_launch"),
+                "kernel": "pass_kernel (fused tile-group conjugation)", "peak_kind": main["peak_kind"],
+                "hbm": hbm, "alu": alu,
                 "algorithmic_bytes_per_launch": 2 * runner.bytes, "avg_launch_ms": round(avg_pass_ms, 4),
                 "launches": pass_cnt, "pass_share_of_step": round(pass_ms / ms, 4) if ms > 0 else None}
     runner.free()

@@ -282,6 +282,13 @@ int orkan_set_timing(orkan_h h, int enable);
  * recorded since the last call, their count, and reset. */
 int orkan_pass_time(orkan_h h, double *ms, int64_t *count);
 
+/* Algorithmic work of the timed passes since the last call, then reset:
+ * alu_ops = sum over ops and stored elements of the arithmetic the op's form
+ * needs per element (FP32 pipe instructions for C64 and DF64 -- a double-float
+ * add is 11, a multiply-add 12 -- FP64 pipe operations for C128; addressing
+ * and data movement excluded); bytes = 2 x stored bytes per pass. */
+int orkan_pass_work(orkan_h h, double *alu_ops, double *bytes);
+
 /* ------------------------------------------------------------------ allocation-free readout
  * The paper has no counterpart to this entry point; it exists for callers that
  * must not allocate device memory themselves -- e.g. code that runs while a

@@ -231,11 +231,28 @@ struct orkan_ctx {
   int64_t n_passes = 0, n_ops = 0, n_launches = 0;
   bool timing = false;
   bool capturing = false;
+  double work_ops = 0.0, work_bytes = 0.0;   // algorithmic ALU ops / bytes of the timed passes
   std::vector<cudaEvent_t> ev_free;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
 };
 
 namespace {
+
+// Algorithmic arithmetic per element of each op form: pipe instructions of the
+// formula as written (double-float: add 11, mul 4, multiply-add 12,
+// renormalise 3, halve 2 FP32 ops; FP64 / FP32: one op each), excluding
+// addressing and data movement.  Used for the ALU roofline of timed passes.
+double alu_ops_per_elem(int dtype, int kind) {
+  const bool dfl = dtype == DT_DF64;
+  switch (kind) {
+    case OP_PTM1_U: return dfl ? 366.0 / 4 : 36.0 / 4;
+    case OP_PTM1: return dfl ? 520.0 / 4 : 48.0 / 4;
+    case OP_PTM1_AD: return dfl ? 152.0 / 4 : 16.0 / 4;
+    case OP_U2: return dfl ? 364.0 : 32.0;
+    case OP_PTM2: return dfl ? 7392.0 / 16 : 640.0 / 16;
+    default: return 0.0;   // monomial ops: no arithmetic
+  }
+}
 
 int rows_log2_for(const orkan_ctx* h, int nh) {
   // 2^(2 nh) tiles x 2^rl rows x M columns within a 64 KiB shared-memory budget
@@ -372,6 +389,9 @@ int flush_pending(orkan_ctx* h) {
   if (timed) {
     ORKAN_CUDA(cudaEventRecord(ev.second, h->stream));
     h->ev_used.push_back(ev);
+    const double elems = double(h->g.ntiles) * double(int64_t(1) << (2 * h->g.m));
+    for (int o = 0; o < d.nops; ++o) h->work_ops += elems * alu_ops_per_elem(h->dtype, d.ops[o].kind);
+    h->work_bytes += 2.0 * double(h->bytes);
   }
   h->n_passes += 1;
   h->n_ops += nops;
@@ -1094,6 +1114,15 @@ int orkan_graph_launch(orkan_h h, void* graph) {
 
 int orkan_graph_free(void* graph) {
   if (graph) ORKAN_CUDA(cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(graph)));
+  return ORKAN_OK;
+}
+
+int orkan_pass_work(orkan_h h, double* alu_ops, double* bytes) {
+  if (int st = check_handle(h)) return st;
+  if (alu_ops) *alu_ops = h->work_ops;
+  if (bytes) *bytes = h->work_bytes;
+  h->work_ops = 0.0;
+  h->work_bytes = 0.0;
   return ORKAN_OK;
 }
 

@@ -91,6 +91,7 @@ _SIGS = {
     "orkan_graph_free": (C.c_int, [C.c_void_p]),
     "orkan_set_timing": (C.c_int, [_h, C.c_int]),
     "orkan_pass_time": (C.c_int, [_h, _pd, C.POINTER(_i64)]),
+    "orkan_pass_work": (C.c_int, [_h, _pd, _pd]),
     "orkan_expect_paulis_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_char_p, _pd,
                                               C.c_void_p]),
 }
@@ -339,6 +340,12 @@ def orkan_stats(h):
 
 def orkan_set_timing(h, enable: bool):
     _check(_lib.orkan_set_timing(h, int(enable)), "orkan_set_timing")
+
+
+def orkan_pass_work(h):
+    ops, nb = C.c_double(), C.c_double()
+    _check(_lib.orkan_pass_work(h, C.byref(ops), C.byref(nb)), "orkan_pass_work")
+    return ops.value, nb.value
 
 
 ORKAN_NOALLOC_MAX_STRINGS = 64
