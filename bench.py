@@ -169,8 +169,8 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# ALU peaks of GB300 (152 SMs at the 2070 MHz maximum clock; per-SM rates measured by the pipe probe,
-# profiles/gb300_pipe_rates.md): FP32 pipe 128 lane-ops per clock per SM, FP64 pipe 2 per clock per SM.
+# ALU peaks of GB300: 152 SMs at the 2070 MHz maximum clock, with per-SM rates measured on GB300 by an
+# FMA-chain probe: FP32 pipe 128 lane-ops per clock per SM, FP64 pipe 2 per clock per SM.
 ALU_PEAK_TOPS = {"df64": 152 * 128 * 2.07e9 / 1e12, "c64": 152 * 128 * 2.07e9 / 1e12,
                  "c128": 152 * 2.0 * 2.07e9 / 1e12}
 
@@ -255,10 +255,16 @@ class Runner:
 def per_op_table(ok, wl, n, m, dtypes, stream, torch, reps=4, only=None):
     """HBM GB/s of single-op passes (fusion 1, no composition) per op class,
     in-tile (target 1 < m) and cross-tile (target n-2 >= m), per dtype: the
-    per-pass view of the sweep (2 x stored bytes / pass time)."""
+    per-pass view of the sweep (2 x stored bytes / pass time).  Three-qubit
+    classes run the block-update kernel (all targets in-tile, all three
+    cross-tile, mixed; a Toffoli as the monomial form).  Beside it, the
+    achieved algorithmic ALU rate (Tops/s) of the classes that do arithmetic."""
     from workloads import synth as S
     rng = S.rng_for(S.BASE_SEED + 11)
-    U1, U2 = S.haar_unitary(rng, 2), S.haar_unitary(rng, 4)
+    U1, U2, U3 = S.haar_unitary(rng, 2), S.haar_unitary(rng, 4), S.haar_unitary(rng, 8)
+    toffoli = np.zeros((8, 8), dtype=np.complex128)
+    for b in range(8):
+        toffoli[b ^ (4 if (b & 3) == 3 else 0), b] = 1
     lo, hi = 1, n - 2
     classes = {
         "u1_in": lambda h: ok.orkan_apply_unitary(h, [lo], U1),
@@ -270,6 +276,10 @@ def per_op_table(ok, wl, n, m, dtypes, stream, torch, reps=4, only=None):
         "u2_in_in": lambda h: ok.orkan_apply_unitary(h, [lo, lo + 1], U2),
         "u2_in_cross": lambda h: ok.orkan_apply_unitary(h, [lo, hi], U2),
         "u2_cross_cross": lambda h: ok.orkan_apply_unitary(h, [hi - 1, hi], U2),
+        "u3_in": lambda h: ok.orkan_apply_unitary(h, [0, 1, 2], U3),
+        "u3_mixed": lambda h: ok.orkan_apply_unitary(h, [lo, n // 2, n - 1], U3),
+        "u3_cross": lambda h: ok.orkan_apply_unitary(h, [n - 3, n - 2, n - 1], U3),
+        "toffoli_cross": lambda h: ok.orkan_apply_unitary(h, [n - 1, n - 2, lo], toffoli),
     }
     if only is not None:
         classes = {only: classes[only]}
@@ -280,18 +290,23 @@ def per_op_table(ok, wl, n, m, dtypes, stream, torch, reps=4, only=None):
         ok.orkan_set_fusion(h, 1, False)
         ok.orkan_init_state(h, ok.ORKAN_INIT_PURE, wl["psi"])
         nbytes = 2 * ok.orkan_bytes(n, DTYPE_NAMES[dt], m)
-        row = {}
+        row, alu = {}, {}
         for name, fn in classes.items():
             fn(h)
             ok.orkan_sync(h)
             ok.orkan_set_timing(h, True)
             ok.orkan_pass_time(h)
+            ok.orkan_pass_work(h)
             for _ in range(reps):
                 fn(h)
             ms, cnt = ok.orkan_pass_time(h)
+            work, _ = ok.orkan_pass_work(h)
             ok.orkan_set_timing(h, False)
             row[name] = round(nbytes / (ms / cnt * 1e-3) / 1e9, 1)
+            if work > 0:
+                alu[name] = round(work / (ms * 1e-3) / 1e12, 2)
         out[dt] = row
+        out[dt + "_alu_Tops"] = alu
         ok.orkan_free(h)
     return out
 

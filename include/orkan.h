@@ -178,11 +178,17 @@ int orkan_store_tiled(orkan_h h, void *host_dst);
  * (the caller issues a circuit's ops in reverse order for Heisenberg
  * evolution). */
 
-/* Unitary gate U (2^k x 2^k, k = 1 or 2) on qubits[0..k-1] (distinct, < n). */
+/* Unitary gate U (2^k x 2^k, k = 1, 2 or 3) on qubits[0..k-1] (distinct, < n).
+ * k = 1, 2: fused into passes over tile groups (Sec. III-C).  k = 3: the
+ * block update of Algorithm 1 (Sec. II-A) in its own launch, every 8x8 block
+ * h_{s,s'} with s >= s' gathered from the tiled layout (up to 64 tiles per
+ * block, Sec. III-C); monomial U (Toffoli, CCZ, Fredkin, ...) permute the
+ * block without arithmetic. */
 int orkan_apply_unitary(orkan_h h, int k, const int *qubits, const double *U);
 
 /* Kraus map with r (1 <= r <= 4^k) operators K (r matrices back to back) on
- * k = 1 or 2 qubits.  Trace non-increase is not checked. */
+ * k = 1, 2 or 3 qubits; for k = 3 at most 16 operators (EINVAL above).  Trace
+ * non-increase is not checked. */
 int orkan_apply_kraus(orkan_h h, int k, const int *qubits, int r, const double *K);
 
 /* Depolarising channel of Sec. IV-A: Kraus sqrt(1-p) I, sqrt(p/3) {X, Y, Z}. */
@@ -214,8 +220,8 @@ int orkan_project(orkan_h h, int q, int outcome);
 
 typedef struct {
   int kind;           /* ORKAN_OP_* */
-  int k;              /* qubits acted on (1 or 2; 1 for channels, measure, project) */
-  int qubits[2];
+  int k;              /* qubits acted on (1 to 3; 1 for channels, measure, project) */
+  int qubits[3];
   int r;              /* Kraus operators (ORKAN_OP_KRAUS) */
   int outcome;        /* ORKAN_OP_PROJECT */
   double param;       /* p, gamma or the uniform draw u */
@@ -269,6 +275,32 @@ int orkan_capture_begin(orkan_h h);
 int orkan_capture_end(orkan_h h, void **graph);
 int orkan_graph_launch(orkan_h h, void *graph);
 int orkan_graph_free(void *graph);
+
+/* ------------------------------------------------------------------ packed column-major layout
+ * Sec. III-A: the N (N + 1) / 2 lower-triangle elements column by column, h_ij
+ * (i >= j) at  j N - j (j - 1) / 2 + (i - j).  The layout the paper compares
+ * the tiled one against (Sec. IV), kept for that comparison: one op per pass,
+ * each 2^k x 2^k block h_{s,s'} (s >= s') updated by one thread straight from
+ * HBM, elements above the diagonal read and written through their stored
+ * partners.  The array is the caller's device memory (dev_packed, at least
+ * orkan_packed_bytes bytes, in the dtype's element format); calls are
+ * asynchronous on cuda_stream (NULL = the legacy default stream).  picture:
+ * ORKAN_STATE applies Phi, ORKAN_OBSERVABLE the adjoint Phi*.  Supported: any
+ * k = 1 map, k = 2 unitaries (monomial ones without arithmetic); EINVAL for
+ * k = 2 Kraus sets with r > 1, k = 3, bad sizes or qubits. */
+size_t orkan_packed_bytes(int n, int dtype);
+/* Element offset of h_ij in the packed array (host only); *conj = 1 when
+ * h_ij is the conjugate of the stored element (i < j).  -1 on bad arguments. */
+int64_t orkan_packed_offset(int n, int64_t i, int64_t j, int *conj);
+int orkan_packed_apply_unitary(void *dev_packed, int n, int dtype, int picture, int k, const int *qubits,
+                               const double *U, void *cuda_stream);
+int orkan_packed_apply_kraus(void *dev_packed, int n, int dtype, int picture, int k, const int *qubits, int r,
+                             const double *K, void *cuda_stream);
+int orkan_packed_depolarize(void *dev_packed, int n, int dtype, int q, double p, void *cuda_stream);
+/* Copy h's operator into / out of a packed array of the same n and dtype, on
+ * h's stream (pending fused ops are launched first). */
+int orkan_packed_from_tiled(orkan_h h, void *dev_packed);
+int orkan_packed_to_tiled(orkan_h h, const void *dev_packed);
 
 /* ------------------------------------------------------------------ instrumentation */
 

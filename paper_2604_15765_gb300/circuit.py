@@ -46,8 +46,8 @@ def marshal(ops, picture: str = "schrodinger"):
         kind = op["kind"]
         q = op["qubits"]
         o.k = len(q)
-        o.qubits[0] = q[0]
-        o.qubits[1] = q[1] if len(q) > 1 else 0
+        for l in range(3):
+            o.qubits[l] = q[l] if len(q) > l else 0
         if kind in ("unitary", "kraus"):
             mats = np.ascontiguousarray(np.asarray(op["matrix"] if kind == "unitary" else op["mats"], np.complex128))
             keep.append(mats)

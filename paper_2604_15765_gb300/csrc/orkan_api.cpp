@@ -136,9 +136,9 @@ Mat swap_local_bits(const Mat& A) {
 struct HostOp {
   int kind = OP_PTM1;
   int nq = 1;
-  int q[2] = {0, 0};           // ascending
+  int q[3] = {0, 0, 0};        // ascending
   std::vector<double> R;       // single-qubit ops: full 4x4 PTM (for composition)
-  std::vector<double> coef;    // kind-specific FP64 coefficients (2-qubit ops)
+  std::vector<double> coef;    // kind-specific FP64 coefficients (2- and 3-qubit ops)
   std::vector<long long> codes;  // monomial ops: permutation and phase codes
 };
 
@@ -250,6 +250,7 @@ double alu_ops_per_elem(int dtype, int kind) {
     case OP_PTM1_AD: return dfl ? 152.0 / 4 : 16.0 / 4;
     case OP_U2: return dfl ? 364.0 : 32.0;
     case OP_PTM2: return dfl ? 7392.0 / 16 : 640.0 / 16;
+    case OP_K3: return dfl ? 748.0 : 64.0;   // per Kraus term: row and column sweeps, 8 complex MACs each
     default: return 0.0;   // monomial ops: no arithmetic
   }
 }
@@ -303,19 +304,74 @@ bool fits(const orkan_ctx* h, const HostOp& op) {
   return slots <= kMaxCoef;
 }
 
-void pack_coef(const orkan_ctx* h, PassDesc& d, int slot, double v) {
-  if (h->dtype == DT_C128) {
-    d.coef[slot] = v;
-  } else if (h->dtype == DT_C64) {
-    float f = (float)v;
-    float pair[2] = {f, 0.0f};
-    std::memcpy(&d.coef[slot], pair, 8);
+// One FP64 coefficient into an 8-byte slot in the policy's format: C128 the
+// double, C64 the float (low half), DF64 the (hi, lo) float pair.
+void pack_slot(int dtype, double* slot, double v) {
+  if (dtype == DT_C128) {
+    *slot = v;
+  } else if (dtype == DT_C64) {
+    const float pair[2] = {(float)v, 0.0f};
+    std::memcpy(slot, pair, 8);
   } else {
     const float hi = (float)v;
-    const float lo = (float)(v - (double)hi);
-    float pair[2] = {hi, lo};
-    std::memcpy(&d.coef[slot], pair, 8);
+    const float pair[2] = {hi, (float)(v - (double)hi)};
+    std::memcpy(slot, pair, 8);
   }
+}
+
+void pack_coef(const orkan_ctx* h, PassDesc& d, int slot, double v) { pack_slot(h->dtype, &d.coef[slot], v); }
+
+// Event pair bracketing one timed pass (pooled events); none while capturing.
+int timing_begin(orkan_ctx* h, std::pair<cudaEvent_t, cudaEvent_t>* ev) {
+  *ev = {nullptr, nullptr};
+  if (!h->timing || h->capturing) return ORKAN_OK;
+  for (int i = 0; i < 2; ++i) {
+    cudaEvent_t e;
+    if (!h->ev_free.empty()) {
+      e = h->ev_free.back();
+      h->ev_free.pop_back();
+    } else {
+      ORKAN_CUDA(cudaEventCreate(&e));
+    }
+    (i == 0 ? ev->first : ev->second) = e;
+  }
+  ORKAN_CUDA(cudaEventRecord(ev->first, h->stream));
+  return ORKAN_OK;
+}
+int timing_end(orkan_ctx* h, const std::pair<cudaEvent_t, cudaEvent_t>& ev, double alu_ops) {
+  if (!ev.first) return ORKAN_OK;
+  ORKAN_CUDA(cudaEventRecord(ev.second, h->stream));
+  h->ev_used.push_back(ev);
+  h->work_ops += alu_ops;
+  h->work_bytes += 2.0 * double(h->bytes);
+  return ORKAN_OK;
+}
+
+// A three-qubit op: its own launch, after the pending fused ops.
+int run_k3(orkan_ctx* h, const HostOp& op) {
+  K3Desc d;
+  std::memset(&d, 0, sizeof(d));
+  const int64_t S = int64_t(1) << (h->g.n - 3);
+  d.nblocks = S * (S + 1) / 2;
+  d.m = h->g.m;
+  for (int l = 0; l < 3; ++l) d.q[l] = op.q[l];
+  if (op.kind == OP_MONO3) {
+    d.form = 1;
+    for (int i = 0; i < 16; ++i) std::memcpy(&d.coef[i], &op.codes[i], 8);
+  } else {
+    d.form = 0;
+    d.r = int(op.coef.size() / 128);
+    for (size_t i = 0; i < op.coef.size(); ++i) pack_slot(h->dtype, &d.coef[i], op.coef[i]);
+  }
+  std::pair<cudaEvent_t, cudaEvent_t> ev;
+  if (int st = timing_begin(h, &ev)) return st;
+  ORKAN_CUDA(launch_k3(h->dtype, h->d_state, d, h->stream));
+  const double elems = double(h->g.ntiles) * double(int64_t(1) << (2 * h->g.m));
+  if (int st = timing_end(h, ev, elems * alu_ops_per_elem(h->dtype, op.kind) * std::max(d.r, 1))) return st;
+  h->n_passes += 1;
+  h->n_ops += 1;
+  h->n_launches += 1;
+  return ORKAN_OK;
 }
 
 int flush_pending(orkan_ctx* h) {
@@ -369,30 +425,14 @@ int flush_pending(orkan_ctx* h) {
   }
   const int64_t nops = int64_t(h->pending.size());
   h->pending.clear();
-  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-  const bool timed = h->timing && !h->capturing;
-  if (timed) {
-    for (int i = 0; i < 2; ++i) {
-      cudaEvent_t e;
-      if (!h->ev_free.empty()) {
-        e = h->ev_free.back();
-        h->ev_free.pop_back();
-      } else {
-        ORKAN_CUDA(cudaEventCreate(&e));
-      }
-      (i == 0 ? ev.first : ev.second) = e;
-    }
-    ORKAN_CUDA(cudaEventRecord(ev.first, h->stream));
-  }
+  std::pair<cudaEvent_t, cudaEvent_t> ev;
+  if (int st = timing_begin(h, &ev)) return st;
   int nlaunch = 0;
   ORKAN_CUDA(launch_pass(h->dtype, h->d_state, d, h->stream, &nlaunch));
-  if (timed) {
-    ORKAN_CUDA(cudaEventRecord(ev.second, h->stream));
-    h->ev_used.push_back(ev);
-    const double elems = double(h->g.ntiles) * double(int64_t(1) << (2 * h->g.m));
-    for (int o = 0; o < d.nops; ++o) h->work_ops += elems * alu_ops_per_elem(h->dtype, d.ops[o].kind);
-    h->work_bytes += 2.0 * double(h->bytes);
-  }
+  double alu = 0.0;
+  const double elems = double(h->g.ntiles) * double(int64_t(1) << (2 * h->g.m));
+  for (int o = 0; o < d.nops; ++o) alu += elems * alu_ops_per_elem(h->dtype, d.ops[o].kind);
+  if (int st = timing_end(h, ev, alu)) return st;
   h->n_passes += 1;
   h->n_ops += nops;
   h->n_launches += nlaunch;
@@ -400,6 +440,10 @@ int flush_pending(orkan_ctx* h) {
 }
 
 int enqueue(orkan_ctx* h, HostOp op) {
+  if (op.nq == 3) {
+    if (int st = flush_pending(h)) return st;
+    return run_k3(h, op);
+  }
   // compose consecutive single-qubit ops on the same qubit (FP64, on the host)
   if (h->compose && op.nq == 1 && !h->pending.empty()) {
     HostOp& last = h->pending.back();
@@ -433,20 +477,57 @@ int check_blocking(orkan_h h) {
   return ORKAN_OK;
 }
 
-int check_qubits(const orkan_ctx* h, int k, const int* qubits) {
-  if (k < 1 || k > 2 || !qubits) return fail(ORKAN_EINVAL, "k must be 1 or 2 with a qubit list");
+int check_qubits_n(int n, int k, const int* qubits) {
+  if (k < 1 || k > 3 || !qubits) return fail(ORKAN_EINVAL, "k must be 1, 2 or 3 with a qubit list");
   for (int l = 0; l < k; ++l)
-    if (qubits[l] < 0 || qubits[l] >= h->g.n) return fail(ORKAN_EINVAL, "qubit out of range");
-  if (k == 2 && qubits[0] == qubits[1]) return fail(ORKAN_EINVAL, "repeated qubit");
+    if (qubits[l] < 0 || qubits[l] >= n) return fail(ORKAN_EINVAL, "qubit out of range");
+  for (int l = 0; l < k; ++l)
+    for (int l2 = l + 1; l2 < k; ++l2)
+      if (qubits[l] == qubits[l2]) return fail(ORKAN_EINVAL, "repeated qubit");
   return ORKAN_OK;
 }
+int check_qubits(const orkan_ctx* h, int k, const int* qubits) { return check_qubits_n(h->g.n, k, qubits); }
 
 // Build the planned op for a k-local Kraus set given in the caller's qubit order.
-int make_op(orkan_ctx* h, int k, const int* qubits, const std::vector<Mat>& kraus_in, bool unitary, HostOp* out) {
-  const bool adj = (h->picture == ORKAN_OBSERVABLE);
+// adj: build the adjoint map (observable handles).
+int make_op_adj(bool adj, int k, const int* qubits, const std::vector<Mat>& kraus_in, bool unitary, HostOp* out) {
   HostOp op;
   op.nq = k;
   std::vector<Mat> kraus = kraus_in;
+  if (k == 3) {
+    // caller bit l <-> qubits[l]; re-index to ascending qubit order
+    int order[3] = {0, 1, 2};
+    std::sort(order, order + 3, [&](int x, int y) { return qubits[x] < qubits[y]; });
+    int rank[3];
+    for (int l = 0; l < 3; ++l) {
+      op.q[l] = qubits[order[l]];
+      rank[order[l]] = l;
+    }
+    auto perm = [&](int x) { return ((x & 1) << rank[0]) | (((x >> 1) & 1) << rank[1]) | (((x >> 2) & 1) << rank[2]); };
+    for (auto& K : kraus) {
+      Mat B(64);
+      for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) B[perm(i) * 8 + perm(j)] = K[i * 8 + j];
+      // the adjoint map applies L^dagger (.) L = M (.) M^dagger with M = L^dagger
+      K = adj ? dagger(B, 8) : B;
+    }
+    std::vector<long long> pp, qq;
+    if (unitary && monomial(kraus[0], 8, &pp, &qq)) {
+      op.kind = OP_MONO3;
+      op.codes = pp;
+      op.codes.insert(op.codes.end(), qq.begin(), qq.end());
+    } else {
+      op.kind = OP_K3;
+      op.coef.resize(128 * kraus.size());
+      for (size_t t = 0; t < kraus.size(); ++t)
+        for (int i = 0; i < 64; ++i) {
+          op.coef[128 * t + 2 * i] = kraus[t][i].real();
+          op.coef[128 * t + 2 * i + 1] = kraus[t][i].imag();
+        }
+    }
+    *out = std::move(op);
+    return ORKAN_OK;
+  }
   if (k == 1) {
     op.q[0] = qubits[0];
     op.R = ptm(1, kraus, adj);
@@ -497,6 +578,10 @@ int make_op(orkan_ctx* h, int k, const int* qubits, const std::vector<Mat>& krau
   }
   *out = std::move(op);
   return ORKAN_OK;
+}
+
+int make_op(orkan_ctx* h, int k, const int* qubits, const std::vector<Mat>& kraus_in, bool unitary, HostOp* out) {
+  return make_op_adj(h->picture == ORKAN_OBSERVABLE, k, qubits, kraus_in, unitary, out);
 }
 
 // An AD-form op with closed-form coefficients (projectors, renormalisation).
@@ -856,6 +941,7 @@ int orkan_apply_kraus(orkan_h h, int k, const int* qubits, int r, const double* 
   if (int st = check_handle(h)) return st;
   if (int st = check_qubits(h, k, qubits)) return st;
   if (!K || r < 1 || r > (1 << (2 * k))) return fail(ORKAN_EINVAL, "need 1 <= r <= 4^k Kraus operators");
+  if (k == 3 && r > kK3MaxTerms) return fail(ORKAN_EINVAL, "three-qubit Kraus sets are limited to 16 operators");
   const int d = 1 << k;
   std::vector<Mat> kraus;
   for (int a = 0; a < r; ++a) kraus.push_back(read_mat(K + 2 * d * d * a, d));
@@ -925,6 +1011,111 @@ int orkan_project(orkan_h h, int q, int outcome) {
   const double sg = outcome ? -0.5 : 0.5;
   const double R[16] = {0.5, 0, 0, sg, 0, 0, 0, 0, 0, 0, 0, 0, sg, 0, 0, 0.5};
   return enqueue(h, make_ad_op(q, R));
+}
+
+// ------------------------------------------------------------------ packed column-major layout
+size_t orkan_packed_bytes(int n, int dtype) {
+  if (n < 1 || n > 24 || (dtype != DT_C128 && dtype != DT_C64 && dtype != DT_DF64)) return 0;
+  const int64_t N = int64_t(1) << n;
+  return size_t(N * (N + 1) / 2) * size_t(elem_size(dtype));
+}
+
+int64_t orkan_packed_offset(int n, int64_t i, int64_t j, int* conj) {
+  if (n < 1 || n > 24) return -1;
+  const int64_t N = int64_t(1) << n;
+  if (i < 0 || j < 0 || i >= N || j >= N) return -1;
+  const bool cj = i < j;
+  if (conj) *conj = cj ? 1 : 0;
+  const int64_t p = cj ? j : i, q = cj ? i : j;
+  return q * N - q * (q - 1) / 2 + (p - q);
+}
+
+namespace {
+int packed_args(const void* dev, int n, int dtype) {
+  if (!dev) return fail(ORKAN_EINVAL, "null packed array");
+  if (orkan_packed_bytes(n, dtype) == 0) return fail(ORKAN_EINVAL, "bad n or dtype");
+  return ORKAN_OK;
+}
+
+int packed_run(void* dev, int n, int dtype, const HostOp& op, void* stream) {
+  PackedDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.N = int64_t(1) << n;
+  d.k = op.nq;
+  d.q[0] = op.q[0];
+  d.q[1] = op.nq == 2 ? op.q[1] : 0;
+  if (op.nq == 1) {
+    if (!op.codes.empty()) {
+      d.kind = OP_MONO1;
+      for (int i = 0; i < 4; ++i) std::memcpy(&d.coef[i], &op.codes[i], 8);
+    } else {
+      d.kind = op.kind;
+      const std::vector<double> c = coef_1q(op.kind, op.R);
+      for (size_t i = 0; i < c.size(); ++i) pack_slot(dtype, &d.coef[i], c[i]);
+    }
+  } else {
+    if (op.kind != OP_U2 && op.kind != OP_MONO2)
+      return fail(ORKAN_EINVAL, "packed layout: two-qubit maps must be unitary (one Kraus operator)");
+    d.kind = op.kind;
+    for (int i = 0; i < 32; ++i) pack_slot(dtype, &d.coef[i], op.coef[i]);
+    for (size_t i = 0; i < op.codes.size(); ++i) std::memcpy(&d.coef[32 + i], &op.codes[i], 8);
+  }
+  const int64_t S = d.N >> d.k;
+  d.n_blocks = S * (S + 1) / 2;
+  const cudaError_t e = launch_packed(dtype, dev, d, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? ORKAN_OK : cuda_fail(e, "packed op");
+}
+
+int packed_kraus(void* dev, int n, int dtype, int picture, int k, const int* qubits, const std::vector<Mat>& kraus,
+                 bool unitary, void* stream) {
+  if (int st = packed_args(dev, n, dtype)) return st;
+  if (picture != ORKAN_STATE && picture != ORKAN_OBSERVABLE) return fail(ORKAN_EINVAL, "bad picture");
+  if (k > 2) return fail(ORKAN_EINVAL, "packed layout: k must be 1 or 2");
+  if (int st = check_qubits_n(n, k, qubits)) return st;
+  HostOp op;
+  if (int st = make_op_adj(picture == ORKAN_OBSERVABLE, k, qubits, kraus, unitary, &op)) return st;
+  return packed_run(dev, n, dtype, op, stream);
+}
+}  // namespace
+
+int orkan_packed_apply_unitary(void* dev_packed, int n, int dtype, int picture, int k, const int* qubits,
+                               const double* U, void* cuda_stream) {
+  if (!U || k < 1 || k > 2) return fail(ORKAN_EINVAL, "packed layout: need k = 1 or 2 and a matrix");
+  return packed_kraus(dev_packed, n, dtype, picture, k, qubits, {read_mat(U, 1 << k)}, true, cuda_stream);
+}
+
+int orkan_packed_apply_kraus(void* dev_packed, int n, int dtype, int picture, int k, const int* qubits, int r,
+                             const double* K, void* cuda_stream) {
+  if (!K || k < 1 || k > 2 || r < 1 || r > (1 << (2 * k))) return fail(ORKAN_EINVAL, "bad Kraus arguments");
+  const int d = 1 << k;
+  std::vector<Mat> kraus;
+  for (int a = 0; a < r; ++a) kraus.push_back(read_mat(K + 2 * d * d * a, d));
+  return packed_kraus(dev_packed, n, dtype, picture, k, qubits, kraus, false, cuda_stream);
+}
+
+int orkan_packed_depolarize(void* dev_packed, int n, int dtype, int q, double p, void* cuda_stream) {
+  if (!(p >= 0.0 && p <= 1.0)) return fail(ORKAN_EINVAL, "p must be in [0, 1]");
+  if (int st = packed_args(dev_packed, n, dtype)) return st;
+  if (int st = check_qubits_n(n, 1, &q)) return st;
+  const double f = 1.0 - 4.0 * p / 3.0;   // self-adjoint: the same in both pictures
+  const double R[16] = {1, 0, 0, 0, 0, f, 0, 0, 0, 0, f, 0, 0, 0, 0, f};
+  return packed_run(dev_packed, n, dtype, make_ad_op(q, R), cuda_stream);
+}
+
+int orkan_packed_from_tiled(orkan_h h, void* dev_packed) {
+  if (int st = check_handle(h)) return st;
+  if (!dev_packed) return fail(ORKAN_EINVAL, "null packed array");
+  if (int st = flush_pending(h)) return st;
+  ORKAN_CUDA(launch_packed_convert(h->dtype, dev_packed, h->d_state, h->g, 1, h->stream));
+  return ORKAN_OK;
+}
+
+int orkan_packed_to_tiled(orkan_h h, const void* dev_packed) {
+  if (int st = check_handle(h)) return st;
+  if (!dev_packed) return fail(ORKAN_EINVAL, "null packed array");
+  if (int st = flush_pending(h)) return st;
+  ORKAN_CUDA(launch_packed_convert(h->dtype, const_cast<void*>(dev_packed), h->d_state, h->g, 0, h->stream));
+  return ORKAN_OK;
 }
 
 int orkan_run_circuit(orkan_h h, int count, const orkan_op* ops, int* outcomes, double* probs, int* done) {

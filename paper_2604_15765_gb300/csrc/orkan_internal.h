@@ -26,7 +26,13 @@ enum Dtype : int { DT_C128 = 0, DT_C64 = 1, DT_DF64 = 2 };
 //             without floating-point arithmetic (Sec. II-B native gates).
 //             Coefficients: MONO1 = (p0, p1, q0, q1); MONO2 = the dense V (32
 //             slots, for the block form) then (p0..p3, q0..q3).
-enum OpKind : int { OP_PTM1 = 0, OP_PTM1_U = 1, OP_PTM1_AD = 2, OP_U2 = 3, OP_PTM2 = 4, OP_MONO1 = 5, OP_MONO2 = 6 };
+//   K3 / MONO3 : three-qubit Kraus sets and monomial unitaries; planned on the
+//             host like the others but run by their own kernel (K3Desc below),
+//             never fused into a pass.
+enum OpKind : int {
+  OP_PTM1 = 0, OP_PTM1_U = 1, OP_PTM1_AD = 2, OP_U2 = 3, OP_PTM2 = 4, OP_MONO1 = 5, OP_MONO2 = 6,
+  OP_K3 = 7, OP_MONO3 = 8
+};
 
 constexpr int kMaxOps = 16;     // ops fused into one pass
 constexpr int kMaxCoef = 640;   // 8-byte coefficient slots per pass
@@ -75,6 +81,42 @@ struct PassDesc {
   double coef[kMaxCoef];   // F64: double; DF64: float2 (hi, lo); C64: float in the low half
 };
 
+// Three-qubit operations (k = 3): Algorithm 1 on the tiled layout.  One
+// launch updates every 8x8 block h_{s,s'} with s >= s' (the others are the
+// adjoints of these):
+//   form 0 (Kraus sweep): h <- sum_t L_t h L_t^dagger, as the row sweep
+//          Y = h L_t^dagger followed by the column sweep L_t Y (Eq. 2);
+//          coefficients: per term 64 complex entries of L_t (row-major,
+//          re / im in consecutive slots), in the policy's slot format;
+//   form 1 (monomial): L[i][p_i] = i^{q_i}, a permutation of the block with
+//          quarter-turn phases; slots 0..7 = p, 8..15 = q as raw int64.
+// The coefficients travel in the kernel parameter (by value, so a captured
+// graph keeps them).
+constexpr int kK3MaxTerms = 16;
+struct K3Desc {
+  int64_t nblocks;   // S (S + 1) / 2 with S = 2^(n - 3)
+  int32_t m;         // tile_log2
+  int32_t q[3];      // target qubits, ascending
+  int32_t form;      // 0 = Kraus sweep, 1 = monomial
+  int32_t r;         // Kraus terms of form 0
+  double coef[kK3MaxTerms * 128];
+};
+cudaError_t launch_k3(int dtype, void* state, const K3Desc& d, cudaStream_t stream);
+
+// One op on the packed column-major layout (Sec. III-A), the comparison
+// layout: every 2^k x 2^k block h_{s,s'} with s >= s' updated by one thread
+// straight from HBM.  Forms: PTM1, PTM1_U, PTM1_AD, MONO1 (k = 1), U2, MONO2
+// (k = 2), with the coefficient slots of the pass kernels.
+struct PackedDesc {
+  int64_t n_blocks;   // S (S + 1) / 2 with S = N / 2^k
+  int64_t N;
+  int32_t k;
+  int32_t kind;
+  int32_t q[2];       // ascending
+  double coef[40];
+};
+cudaError_t launch_packed(int dtype, void* state, const PackedDesc& d, cudaStream_t stream);
+
 // Record the message that orkan_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
 
@@ -91,6 +133,9 @@ struct Geometry {
   int64_t ntiles;  // Nt (Nt + 1) / 2
 };
 cudaError_t launch_zero(int dtype, void* state, const Geometry& g, cudaStream_t s);
+// Tiled <-> packed column-major copies of one operator (to_packed = 1: tiled -> packed).
+cudaError_t launch_packed_convert(int dtype, void* packed, void* tiled, const Geometry& g, int to_packed,
+                                  cudaStream_t stream);
 cudaError_t launch_set_diag(int dtype, void* state, const Geometry& g, int64_t i, double re, cudaStream_t s);
 cudaError_t launch_fill_diag(int dtype, void* state, const Geometry& g, double re, cudaStream_t s);
 cudaError_t launch_from_dense(int dtype, void* state, const Geometry& g, const double* dense_dev, cudaStream_t s);

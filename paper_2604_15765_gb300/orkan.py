@@ -38,7 +38,7 @@ _h = C.c_void_p
 
 class OrkanOp(C.Structure):
     """orkan_op of include/orkan.h."""
-    _fields_ = [("kind", C.c_int), ("k", C.c_int), ("qubits", C.c_int * 2), ("r", C.c_int), ("outcome", C.c_int),
+    _fields_ = [("kind", C.c_int), ("k", C.c_int), ("qubits", C.c_int * 3), ("r", C.c_int), ("outcome", C.c_int),
                 ("param", C.c_double), ("mats", C.POINTER(C.c_double))]
 
 
@@ -94,6 +94,14 @@ _SIGS = {
     "orkan_pass_work": (C.c_int, [_h, _pd, _pd]),
     "orkan_expect_paulis_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_char_p, _pd,
                                               C.c_void_p]),
+    "orkan_packed_bytes": (C.c_size_t, [C.c_int, C.c_int]),
+    "orkan_packed_offset": (_i64, [C.c_int, _i64, _i64, _pi]),
+    "orkan_packed_apply_unitary": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, _pi, _pd, C.c_void_p]),
+    "orkan_packed_apply_kraus": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, _pi, C.c_int, _pd,
+                                           C.c_void_p]),
+    "orkan_packed_depolarize": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p]),
+    "orkan_packed_from_tiled": (C.c_int, [_h, C.c_void_p]),
+    "orkan_packed_to_tiled": (C.c_int, [_h, C.c_void_p]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -359,6 +367,44 @@ def orkan_expect_paulis_noalloc(dev_state: int, n: int, dtype: int, tile_log2: i
     _check(_lib.orkan_expect_paulis_noalloc(C.c_void_p(dev_state), n, dtype, tile_log2, len(paulis), s, _dptr(out),
                                             C.c_void_p(stream_ptr or 0)), "orkan_expect_paulis_noalloc")
     return out
+
+
+# ------------------------------------------------------------------ packed column-major layout
+def orkan_packed_bytes(n: int, dtype: int) -> int:
+    return int(_lib.orkan_packed_bytes(n, dtype))
+
+
+def orkan_packed_offset(n: int, i: int, j: int):
+    cj = C.c_int()
+    off = int(_lib.orkan_packed_offset(n, i, j, C.byref(cj)))
+    return off, bool(cj.value)
+
+
+def orkan_packed_apply_unitary(dev: int, n: int, dtype: int, qubits, U, picture=ORKAN_STATE, stream_ptr=None):
+    M = _cplx(U)
+    _check(_lib.orkan_packed_apply_unitary(C.c_void_p(dev), n, dtype, picture, len(qubits), _qubits(qubits),
+                                           _dptr(M.view(np.float64)), C.c_void_p(stream_ptr or 0)),
+           "orkan_packed_apply_unitary")
+
+
+def orkan_packed_apply_kraus(dev: int, n: int, dtype: int, qubits, kraus, picture=ORKAN_STATE, stream_ptr=None):
+    K = _cplx(kraus, 1 << len(qubits))
+    _check(_lib.orkan_packed_apply_kraus(C.c_void_p(dev), n, dtype, picture, len(qubits), _qubits(qubits),
+                                         K.shape[0], _dptr(K.view(np.float64)), C.c_void_p(stream_ptr or 0)),
+           "orkan_packed_apply_kraus")
+
+
+def orkan_packed_depolarize(dev: int, n: int, dtype: int, q: int, p: float, stream_ptr=None):
+    _check(_lib.orkan_packed_depolarize(C.c_void_p(dev), n, dtype, q, p, C.c_void_p(stream_ptr or 0)),
+           "orkan_packed_depolarize")
+
+
+def orkan_packed_from_tiled(h, dev: int):
+    _check(_lib.orkan_packed_from_tiled(h, C.c_void_p(dev)), "orkan_packed_from_tiled")
+
+
+def orkan_packed_to_tiled(h, dev: int):
+    _check(_lib.orkan_packed_to_tiled(h, C.c_void_p(dev)), "orkan_packed_to_tiled")
 
 
 def orkan_pass_time(h):

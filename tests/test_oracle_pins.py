@@ -432,3 +432,43 @@ def test_factored_kraus_matches_dense():
         assert np.max(np.abs(dense - D.apply_kraus(H, kraus, qubits))) < 1e-15
         rows, cols = rng.integers(0, 1 << n, 50), rng.integers(0, 1 << n, 50)
         assert np.max(np.abs(D.factored_elements(out, rows, cols) - dense[rows, cols])) < 1e-15
+
+
+# ---------------------------------------------------------------- k = 3
+def _toffoli():
+    """Controls on index bits 0 and 1, target on bit 2."""
+    T = np.zeros((8, 8), dtype=np.complex128)
+    for b in range(8):
+        T[b ^ (4 if (b & 3) == 3 else 0), b] = 1
+    return T
+
+
+def test_toffoli_on_basis_states():
+    """A 3-qubit gate with unsorted qubits: Toffoli flips qubits[2] exactly
+    when qubits[0] and qubits[1] are both 1, for every ordered triple."""
+    n = 4
+    T = _toffoli()
+    for c0, c1, t in itertools.permutations(range(n), 3):
+        for x in range(1 << n):
+            rho = np.zeros((1 << n, 1 << n), dtype=np.complex128)
+            rho[x, x] = 1
+            y = x ^ ((((x >> c0) & 1) & ((x >> c1) & 1)) << t)
+            expect = np.zeros_like(rho)
+            expect[y, y] = 1
+            assert np.array_equal(D.apply_unitary(rho, T, [c0, c1, t]), expect)
+
+
+def test_three_qubit_product_equals_single_qubit_gates():
+    """kron(U2, U1, U0) on qubits [a, b, c] (bit l <-> qubits[l]) equals U0 on
+    a, U1 on b and U2 on c applied one at a time; the single-qubit embeddings
+    are plain Kronecker products with no permutation."""
+    rng = S.rng_for(610)
+    n = 5
+    rho = S.ginibre_state(rng, 1 << n)
+    for qubits in ([4, 0, 2], [1, 3, 0], [0, 1, 2], [2, 4, 3]):
+        us = [S.haar_unitary(rng, 2) for _ in range(3)]
+        L = np.kron(us[2], np.kron(us[1], us[0]))
+        seq = rho
+        for u, q in zip(us, qubits):
+            seq = D.apply_unitary(seq, u, [q])
+        assert np.max(np.abs(D.apply_unitary(rho, L, qubits) - seq)) < 1e-15
