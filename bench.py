@@ -56,7 +56,7 @@ def parse_args(argv=None):
     p.add_argument("--no-variants", action="store_true", help="skip the c128 / c64 / unfused comparison runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=20.0)
-    p.add_argument("--workload", choices=["sweep", "serving", "brickwork", "precision"], default="sweep")
+    p.add_argument("--workload", choices=["sweep", "serving", "brickwork", "precision", "paper"], default="sweep")
     p.add_argument("--depth", type=int, default=40)
     p.add_argument("--serve-requests", type=int, default=160,
                    help="requests in the serving sample of the default run (the serving workload uses 5000)")
@@ -390,6 +390,92 @@ def brickwork_study(ok, circuit, torch, stream, n, dt, depth):
     return out
 
 
+def paper_study(ok, torch, stream, dtypes=("c128", "df64"), ns=(6, 8, 10, 12, 13, 14, 15, 16), min_ms=40.0):
+    """The paper's own experiments (Sec. IV and its appendix): the depolarising
+    channel with p = 0.1, Pauli X, Hadamard and CNOT; time per execution
+    averaged over all qubit positions (all ordered pairs for CNOT), a layer
+    applying the op at every position in turn to a continuously evolved random
+    hermitian operator (a 16-term Pauli sum: neither positive nor normalised),
+    after one warm-up layer.  Layouts: packed column-major and tiled (m = 5)
+    with one op per pass -- the paper's comparison -- and tiled with fusion
+    (8 ops, composition).  Effective bandwidth as the paper defines it: stored
+    bytes / time per op, in GiB/s."""
+    from workloads import synth as S
+    had = np.array([[1, 1], [1, -1]], dtype=np.complex128) / np.sqrt(2)
+    xg = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    cnot = np.eye(4, dtype=np.complex128)[[0, 3, 2, 1]]
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    cur = torch.cuda.current_stream()
+
+    def timed(layer):
+        layer()                                   # warm-up layer
+        cur.synchronize()
+        reps = 1
+        while True:
+            ev[0].record(cur)
+            for _ in range(reps):
+                layer()
+            ev[1].record(cur)
+            ev[1].synchronize()
+            ms = ev[0].elapsed_time(ev[1])
+            if ms >= min_ms or reps >= 64:
+                return ms / reps
+            reps = min(64, max(2 * reps, int(reps * min_ms / max(ms, 1e-3)) + 1))
+
+    out = {}
+    for dt in dtypes:
+        code = DTYPE_NAMES[dt]
+        table = {}
+        for n in ns:
+            rng = S.rng_for(S.BASE_SEED + 12 + n)
+            strings, coeffs = S.random_pauli_sum(rng, n, 16)
+            pos1 = [[q] for q in range(n)]
+            pos2 = [[c, t] for c in range(n) for t in range(n) if c != t]
+            cases = {"depolarize": pos1, "x": pos1, "hadamard": pos1, "cnot": pos2}
+            ht = ok.orkan_alloc(n, code, 5)
+            buf = torch.empty(ok.orkan_packed_bytes(n, code), dtype=torch.uint8, device="cuda")
+            ok.orkan_set_stream(ht, stream)
+            ok.orkan_init_observable(ht, strings, coeffs)
+            ok.orkan_set_picture(ht, ok.ORKAN_STATE)
+            ok.orkan_packed_from_tiled(ht, buf.data_ptr())   # both layouts start from the same operator
+            dev = buf.data_ptr()
+            tiled_bytes = ok.orkan_bytes(n, code, 5)
+            packed_bytes = ok.orkan_packed_bytes(n, code)
+            row = {"tiled_bytes": tiled_bytes, "packed_bytes": packed_bytes}
+            for name, pos in cases.items():
+                def tiled_layer(f, c, pos=pos, name=name):
+                    ok.orkan_set_fusion(ht, f, c)
+                    for q in pos:
+                        if name == "depolarize":
+                            ok.orkan_depolarize(ht, q[0], 0.1)
+                        else:
+                            ok.orkan_apply_unitary(ht, q, {"x": xg, "hadamard": had, "cnot": cnot}[name])
+                    ok.orkan_flush(ht)
+
+                def packed_layer(pos=pos, name=name):
+                    for q in pos:
+                        if name == "depolarize":
+                            ok.orkan_packed_depolarize(dev, n, code, q[0], 0.1, stream)
+                        else:
+                            ok.orkan_packed_apply_unitary(dev, n, code, q, {"x": xg, "hadamard": had, "cnot": cnot}[name],
+                                                          ok.ORKAN_STATE, stream)
+                res = {}
+                for label, fn, nbytes in (("packed", packed_layer, packed_bytes),
+                                          ("tiled", lambda: tiled_layer(1, False), tiled_bytes),
+                                          ("tiled_fused", lambda: tiled_layer(8, True), tiled_bytes)):
+                    us = timed(fn) * 1e3 / len(pos)
+                    res[label + "_us"] = round(us, 3)
+                    res[label + "_GiBps"] = round(nbytes / (us * 1e-6) / 2 ** 30, 1)
+                res["tiled_speedup_over_packed"] = round(res["packed_us"] / res["tiled_us"], 3)
+                row[name] = res
+            ok.orkan_free(ht)
+            del buf
+            torch.cuda.empty_cache()
+            table[str(n)] = row
+        out[dt] = table
+    return out
+
+
 def precision_study(ok, circuit, torch, stream, depth):
     """Trace distance / max |delta| / Frobenius / trace error of the storage
     and arithmetic forms on the depth-40 noisy brickwork: against the CPU
@@ -572,9 +658,19 @@ def main(argv=None):
         tab = per_op_table(ok, wl, n, m, (args.dtype,), stream, torch, reps=args.steps, only=args.op_class)
         print(json.dumps({"op_class": args.op_class, "dtype": args.dtype, "n": n, "pass_GBps": tab[args.dtype]}))
         return 0
-    if args.workload in ("brickwork", "precision"):
-        import numpy  # noqa: F401
-        if args.workload == "brickwork":
+    if args.workload in ("brickwork", "precision", "paper"):
+        if args.workload == "paper":
+            ps = paper_study(ok, torch, stream)
+            big = ps["df64"]["16"]
+            ops = 3 * 16 + 16 * 15   # depolarising, X and Hadamard on 16 targets, CNOT on 240 ordered pairs
+            secs = sum(big[k]["tiled_fused_us"] * (16 * 15 if k == "cnot" else 16) for k in
+                       ("depolarize", "x", "hadamard", "cnot")) * 1e-6
+            val = round(ops / secs, 2)
+            cfg = {"workload": "the paper's experiments: depolarising p=0.1, X, Hadamard, CNOT over all positions, "
+                               "n=6..16, packed column-major vs tiled (m=5) one op per pass vs tiled fused; value = "
+                               "tiled fused ops/s over the four experiments at n=16 in df64"}
+            extra = {"paper": ps}
+        elif args.workload == "brickwork":
             bw = brickwork_study(ok, circuit, torch, stream, 16 if args.n == 14 else args.n, args.dtype, args.depth)
             val = bw["autotuned"]["ops_per_s"]
             cfg = {"workload": f"noisy brickwork n={bw['n']}, depth {args.depth}, autotuned vs unfused",

@@ -14,8 +14,10 @@ Everything here is plain NumPy / SciPy in complex128 on the full dense
 * :mod:`oracle.tiled`  -- the tiled lower-triangle storage format of
   Sec. III-B (Table I sizes, tile order, element order), the bit insertion
   of Subroutine 1 and the tiled mean-value formula of Sec. III-C.
+* :mod:`oracle.packed` -- the packed column-major lower-triangle format of
+  Sec. III-A (the layout the tiled one is compared against).
 
 Parity status: every function is pinned by ``tests/test_oracle_pins.py``
 against closed forms, invariants, brute force or the paper's Table I.
 """
-from . import dense, tiled  # noqa: F401
+from . import dense, packed, tiled  # noqa: F401

@@ -38,6 +38,10 @@ struct PolF64 {
   static __device__ __forceinline__ Real add(Real a, Real b) { return a + b; }
   static __device__ __forceinline__ Real sub(Real a, Real b) { return a - b; }
   static __device__ __forceinline__ Real neg(Real a) { return -a; }
+  // -a by flipping the sign bit with integer ops (no FP64 pipe instruction)
+  static __device__ __forceinline__ Real flip(Real a) {
+    return __hiloint2double(__double2hiint(a) ^ int(0x80000000u), __double2loint(a));
+  }
   static __device__ __forceinline__ Real half(Real a) { return 0.5 * a; }
   static __device__ __forceinline__ Real mul(Real x, Coef c) { return x * c; }
   static __device__ __forceinline__ Real mac(Real acc, Real x, Coef c) { return fma(x, c, acc); }
@@ -67,6 +71,7 @@ struct PolF32 {
   static __device__ __forceinline__ Real add(Real a, Real b) { return a + b; }
   static __device__ __forceinline__ Real sub(Real a, Real b) { return a - b; }
   static __device__ __forceinline__ Real neg(Real a) { return -a; }
+  static __device__ __forceinline__ Real flip(Real a) { return __int_as_float(__float_as_int(a) ^ int(0x80000000u)); }
   static __device__ __forceinline__ Real half(Real a) { return 0.5f * a; }
   static __device__ __forceinline__ Real mul(Real x, Coef c) { return x * c; }
   static __device__ __forceinline__ Real mac(Real acc, Real x, Coef c) { return fmaf(x, c, acc); }
@@ -118,6 +123,10 @@ struct PolDF64 {
     return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
   }
   static __device__ __forceinline__ Real neg(Real a) { return {-a.hi, -a.lo}; }
+  static __device__ __forceinline__ Real flip(Real a) {
+    return {__int_as_float(__float_as_int(a.hi) ^ int(0x80000000u)),
+            __int_as_float(__float_as_int(a.lo) ^ int(0x80000000u))};
+  }
   static __device__ __forceinline__ Real sub(Real a, Real b) { return add(a, neg(b)); }
   static __device__ __forceinline__ Real half(Real a) { return {__fmul_rn(0.5f, a.hi), __fmul_rn(0.5f, a.lo)}; }
   // x * c with the exact rounding error of the leading product (TwoProduct by FMA)

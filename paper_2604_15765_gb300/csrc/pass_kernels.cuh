@@ -162,14 +162,15 @@ __device__ __forceinline__ int icoef(const double* cf, int i) {
   return int(reinterpret_cast<const long long*>(cf)[i]);
 }
 
-// z * i^k for k = 0..3: exact (swaps and sign flips of the parts).
+// z * i^k for k = 0..3: exact (swaps and sign-bit flips of the parts, no
+// floating-point instructions).
 template <class P>
 __device__ __forceinline__ Cx<P> rot_i(const Cx<P>& z, int k) {
   switch (k & 3) {
     case 0: return z;
-    case 1: return Cx<P>{P::neg(z.im), z.re};
-    case 2: return Cx<P>{P::neg(z.re), P::neg(z.im)};
-    default: return Cx<P>{z.im, P::neg(z.re)};
+    case 1: return Cx<P>{P::flip(z.im), z.re};
+    case 2: return Cx<P>{P::flip(z.re), P::flip(z.im)};
+    default: return Cx<P>{z.im, P::flip(z.re)};
   }
 }
 
@@ -711,7 +712,7 @@ __device__ __forceinline__ Cx<P> dread(const typename P::Elem* sm, const DMap& m
     return Cx<P>{P::re(e), P::im(e)};
   }
   const auto e = sm[mp.at(y * (y + 1) / 2 + x, c, r)];
-  return Cx<P>{P::re(e), P::neg(P::im(e))};
+  return Cx<P>{P::re(e), P::flip(P::im(e))};
 }
 
 template <class P>
@@ -722,9 +723,9 @@ __device__ __forceinline__ void dwrite(typename P::Elem* sm, const DMap& mp, int
     sm[mp.at(x * (x + 1) / 2 + y, r, c)] = P::make(v.re, v.im);
   } else if (x == y) {
     sm[mp.at(x * (x + 1) / 2 + x, r, c)] = P::make(v.re, v.im);
-    if (r != c) sm[mp.at(x * (x + 1) / 2 + x, c, r)] = P::make(v.re, P::neg(v.im));
+    if (r != c) sm[mp.at(x * (x + 1) / 2 + x, c, r)] = P::make(v.re, P::flip(v.im));
   } else {
-    sm[mp.at(y * (y + 1) / 2 + x, c, r)] = P::make(v.re, P::neg(v.im));
+    sm[mp.at(y * (y + 1) / 2 + x, c, r)] = P::make(v.re, P::flip(v.im));
   }
 }
 

@@ -89,3 +89,33 @@ def test_alloc_without_gpu_reports_no_device():
     with pytest.raises(ok.OrkanError) as e:
         ok.orkan_alloc(4, ok.ORKAN_C128, 5)
     assert e.value.status == ok.ORKAN_ENODEV
+
+
+def test_packed_layout_matches_oracle():
+    from oracle import packed as PK
+    for n in range(1, 12):
+        assert ok.orkan_packed_bytes(n, ok.ORKAN_C128) == PK.packed_elements(n) * 16
+        assert ok.orkan_packed_bytes(n, ok.ORKAN_DF64) == PK.packed_elements(n) * 16
+        assert ok.orkan_packed_bytes(n, ok.ORKAN_C64) == PK.packed_elements(n) * 8
+    assert ok.orkan_packed_bytes(0, ok.ORKAN_C128) == 0
+    assert ok.orkan_packed_bytes(3, 9) == 0
+    for n in (1, 3, 5):
+        for i in range(1 << n):
+            for j in range(1 << n):
+                assert ok.orkan_packed_offset(n, i, j) == PK.packed_offset(i, j, n)
+    assert ok.orkan_packed_offset(3, 8, 0)[0] == -1
+
+
+def test_packed_calls_validate_before_any_launch():
+    """Argument errors are reported without touching a device."""
+    U = np.eye(2, dtype=np.complex128)
+    with pytest.raises(ok.OrkanError):
+        ok.orkan_packed_apply_unitary(0, 3, ok.ORKAN_C128, [0], U)            # null array
+    with pytest.raises(ok.OrkanError):
+        ok.orkan_packed_apply_unitary(64, 3, ok.ORKAN_C128, [3], U)           # qubit out of range
+    with pytest.raises(ok.OrkanError):
+        ok.orkan_packed_apply_unitary(64, 3, ok.ORKAN_C128, [0, 1, 2], np.eye(8))   # k = 3
+    with pytest.raises(ok.OrkanError):
+        ok.orkan_packed_apply_kraus(64, 3, ok.ORKAN_C128, [0, 1], np.stack([np.eye(4) * 0.5] * 2))  # r > 1, k = 2
+    with pytest.raises(ok.OrkanError):
+        ok.orkan_packed_depolarize(64, 3, ok.ORKAN_C128, 0, 1.5)

@@ -472,3 +472,28 @@ def test_three_qubit_product_equals_single_qubit_gates():
         for u, q in zip(us, qubits):
             seq = D.apply_unitary(seq, u, [q])
         assert np.max(np.abs(D.apply_unitary(rho, L, qubits) - seq)) < 1e-15
+
+
+# ---------------------------------------------------------------- packed layout
+def test_packed_layout_by_enumeration():
+    """Sec. III-A: walking the lower triangle column by column visits the
+    offsets 0, 1, 2, ... of the closed form; the storage is N (N + 1) / 2
+    elements (Table I's packed column)."""
+    from oracle import packed as PK
+    for n in range(1, 7):
+        N = 1 << n
+        pos = 0
+        for j in range(N):
+            for i in range(j, N):
+                assert PK.packed_offset(i, j, n) == (pos, False)
+                assert PK.packed_offset(j, i, n) == (pos, i != j)
+                pos += 1
+        assert pos == PK.packed_elements(n) == N * (N + 1) // 2
+    rng = S.rng_for(620)
+    H = S.random_hermitian(rng, 16)
+    buf = PK.to_packed(H)
+    assert buf.size == PK.packed_elements(4)
+    assert np.array_equal(PK.from_packed(buf, 4), H)
+    for i, j in [(3, 1), (1, 3), (15, 0), (0, 15), (7, 7)]:
+        off, cj = PK.packed_offset(i, j, 4)
+        assert (np.conj(buf[off]) if cj else buf[off]) == H[i, j]
