@@ -56,10 +56,15 @@ def parse_args(argv=None):
     p.add_argument("--no-variants", action="store_true", help="skip the c128 / c64 / unfused comparison runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=20.0)
-    p.add_argument("--workload", choices=["sweep", "serving", "brickwork", "precision", "paper"], default="sweep")
+    p.add_argument("--workload", choices=["sweep", "serving", "brickwork", "precision", "paper", "relabel"],
+                   default="sweep")
     p.add_argument("--depth", type=int, default=40)
     p.add_argument("--serve-requests", type=int, default=160,
                    help="requests in the serving sample of the default run (the serving workload uses 5000)")
+    p.add_argument("--paper-sizes", default="6,8,10,12,13,14,15,16", help="qubit counts of the paper study")
+    p.add_argument("--paper-ops", default="depolarize,x,hadamard,cnot", help="experiments of the paper study")
+    p.add_argument("--paper-dtypes", default="c128,df64", help="storage types of the paper study")
+    p.add_argument("--paper-layouts", default="packed,tiled,tiled_fused", help="layouts of the paper study")
     p.add_argument("--op-class", default=None,
                    help="time only single-op passes of one class (u1_in, u2_in_cross, ...) and print their GB/s")
     return p.parse_args(argv)
@@ -265,6 +270,8 @@ def per_op_table(ok, wl, n, m, dtypes, stream, torch, reps=4, only=None):
     toffoli = np.zeros((8, 8), dtype=np.complex128)
     for b in range(8):
         toffoli[b ^ (4 if (b & 3) == 3 else 0), b] = 1
+    xg = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    cnot = np.eye(4, dtype=np.complex128)[[0, 3, 2, 1]]
     lo, hi = 1, n - 2
     classes = {
         "u1_in": lambda h: ok.orkan_apply_unitary(h, [lo], U1),
@@ -276,6 +283,10 @@ def per_op_table(ok, wl, n, m, dtypes, stream, torch, reps=4, only=None):
         "u2_in_in": lambda h: ok.orkan_apply_unitary(h, [lo, lo + 1], U2),
         "u2_in_cross": lambda h: ok.orkan_apply_unitary(h, [lo, hi], U2),
         "u2_cross_cross": lambda h: ok.orkan_apply_unitary(h, [hi - 1, hi], U2),
+        "x_in": lambda h: ok.orkan_apply_unitary(h, [lo], xg),
+        "x_cross": lambda h: ok.orkan_apply_unitary(h, [hi], xg),
+        "cnot_in_cross": lambda h: ok.orkan_apply_unitary(h, [lo, hi], cnot),
+        "cnot_cross_cross": lambda h: ok.orkan_apply_unitary(h, [hi, hi - 1], cnot),
         "u3_in": lambda h: ok.orkan_apply_unitary(h, [0, 1, 2], U3),
         "u3_mixed": lambda h: ok.orkan_apply_unitary(h, [lo, n // 2, n - 1], U3),
         "u3_cross": lambda h: ok.orkan_apply_unitary(h, [n - 3, n - 2, n - 1], U3),
@@ -390,7 +401,8 @@ def brickwork_study(ok, circuit, torch, stream, n, dt, depth):
     return out
 
 
-def paper_study(ok, torch, stream, dtypes=("c128", "df64"), ns=(6, 8, 10, 12, 13, 14, 15, 16), min_ms=40.0):
+def paper_study(ok, torch, stream, dtypes=("c128", "df64"), ns=(6, 8, 10, 12, 13, 14, 15, 16), min_ms=40.0,
+                experiments=("depolarize", "x", "hadamard", "cnot"), layouts=("packed", "tiled", "tiled_fused")):
     """The paper's own experiments (Sec. IV and its appendix): the depolarising
     channel with p = 0.1, Pauli X, Hadamard and CNOT; time per execution
     averaged over all qubit positions (all ordered pairs for CNOT), a layer
@@ -431,7 +443,8 @@ def paper_study(ok, torch, stream, dtypes=("c128", "df64"), ns=(6, 8, 10, 12, 13
             strings, coeffs = S.random_pauli_sum(rng, n, 16)
             pos1 = [[q] for q in range(n)]
             pos2 = [[c, t] for c in range(n) for t in range(n) if c != t]
-            cases = {"depolarize": pos1, "x": pos1, "hadamard": pos1, "cnot": pos2}
+            cases = {k: v for k, v in {"depolarize": pos1, "x": pos1, "hadamard": pos1, "cnot": pos2}.items()
+                     if k in experiments}
             ht = ok.orkan_alloc(n, code, 5)
             buf = torch.empty(ok.orkan_packed_bytes(n, code), dtype=torch.uint8, device="cuda")
             ok.orkan_set_stream(ht, stream)
@@ -463,16 +476,69 @@ def paper_study(ok, torch, stream, dtypes=("c128", "df64"), ns=(6, 8, 10, 12, 13
                 for label, fn, nbytes in (("packed", packed_layer, packed_bytes),
                                           ("tiled", lambda: tiled_layer(1, False), tiled_bytes),
                                           ("tiled_fused", lambda: tiled_layer(8, True), tiled_bytes)):
+                    if label not in layouts:
+                        continue
                     us = timed(fn) * 1e3 / len(pos)
                     res[label + "_us"] = round(us, 3)
                     res[label + "_GiBps"] = round(nbytes / (us * 1e-6) / 2 ** 30, 1)
-                res["tiled_speedup_over_packed"] = round(res["packed_us"] / res["tiled_us"], 3)
+                if "packed_us" in res and "tiled_us" in res:
+                    res["tiled_speedup_over_packed"] = round(res["packed_us"] / res["tiled_us"], 3)
                 row[name] = res
             ok.orkan_free(ht)
             del buf
             torch.cuda.empty_cache()
             table[str(n)] = row
         out[dt] = table
+    return out
+
+
+def relabel_study(ok, circuit, torch, stream, n=16, depth=40, dtypes=("df64", "c64")):
+    """Qubit relabelling on a circuit concentrated on the five highest qubits
+    (Haar 1q on each, Haar 2q on alternating neighbour pairs, depolarising
+    1e-3 on each, per layer): automatic relabelling (the hot qubits swapped
+    into the tile first) against none; same fusion (8 ops, composition)."""
+    from workloads import synth as S
+    rng = S.rng_for(S.BASE_SEED + 13)
+    hot = list(range(n - 5, n))
+    ops = []
+    for layer in range(depth):
+        for q in hot:
+            ops.append(S.op_unitary(S.haar_unitary(rng, 2), [q]))
+        for a in range(layer % 2, 4, 2):
+            ops.append(S.op_unitary(S.haar_unitary(rng, 4), [hot[a], hot[a + 1]]))
+        for q in hot:
+            ops.append(S.op_depolarize(q, 1e-3))
+    psi = S.haar_state_vector(rng, 1 << n)
+    paulis = S.random_pauli_strings(rng, n, 8)
+    arr, keep, _ = circuit.marshal(ops)
+    out = {"n": n, "depth": depth, "ops": len(ops), "hot_qubits": hot}
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    cur = torch.cuda.current_stream()
+    for dt in dtypes:
+        row, res = {}, {}
+        for mode in (0, 1):
+            h = ok.orkan_alloc(n, DTYPE_NAMES[dt], 5)
+            ok.orkan_set_stream(h, stream)
+            ok.orkan_set_fusion(h, 8, True)
+            ok.orkan_set_relabel(h, mode)
+            ok.orkan_init_state(h, ok.ORKAN_INIT_PURE, psi)
+            ok.orkan_sync(h)
+            p0 = ok.orkan_stats(h)["passes"]
+            ev[0].record(cur)
+            ok.orkan_run_circuit(h, arr, 0)
+            ok.orkan_flush(h)
+            ev[1].record(cur)
+            ev[1].synchronize()
+            ms = ev[0].elapsed_time(ev[1])
+            passes = ok.orkan_stats(h)["passes"] - p0
+            res[mode] = np.array([ok.orkan_expect_pauli(h, s) for s in paulis])
+            row["relabel" if mode else "plain"] = {"ms": round(ms, 2), "ops_per_s": round(len(ops) / (ms * 1e-3), 1),
+                                                   "passes": passes, "labels_after": ok.orkan_get_labels(h, n)}
+            ok.orkan_free(h)
+        row["speedup"] = round(row["plain"]["ms"] / row["relabel"]["ms"], 3)
+        row["max_expectation_diff"] = float(np.max(np.abs(res[0] - res[1])))
+        out[dt] = row
+    del keep
     return out
 
 
@@ -658,14 +724,26 @@ def main(argv=None):
         tab = per_op_table(ok, wl, n, m, (args.dtype,), stream, torch, reps=args.steps, only=args.op_class)
         print(json.dumps({"op_class": args.op_class, "dtype": args.dtype, "n": n, "pass_GBps": tab[args.dtype]}))
         return 0
-    if args.workload in ("brickwork", "precision", "paper"):
-        if args.workload == "paper":
-            ps = paper_study(ok, torch, stream)
-            big = ps["df64"]["16"]
+    if args.workload in ("brickwork", "precision", "paper", "relabel"):
+        if args.workload == "relabel":
+            rl = relabel_study(ok, circuit, torch, stream, n=16 if args.n == 14 else args.n, depth=args.depth)
+            val = rl[args.dtype]["relabel"]["ops_per_s"] if args.dtype in rl else rl["df64"]["relabel"]["ops_per_s"]
+            cfg = {"workload": f"circuit on the 5 highest of n={rl['n']} qubits, depth {args.depth}: automatic "
+                               "qubit relabelling vs none", "n": rl["n"], "depth": args.depth}
+            extra = {"relabel": rl}
+        elif args.workload == "paper":
+            ps = paper_study(ok, torch, stream, dtypes=tuple(args.paper_dtypes.split(",")),
+                             ns=tuple(int(x) for x in args.paper_sizes.split(",")),
+                             experiments=tuple(args.paper_ops.split(",")), layouts=tuple(args.paper_layouts.split(",")))
+            full = "16" in ps.get("df64", {}) and all(k in ps["df64"]["16"] for k in ("depolarize", "x", "hadamard", "cnot"))
+            big = ps["df64"]["16"] if full else None
             ops = 3 * 16 + 16 * 15   # depolarising, X and Hadamard on 16 targets, CNOT on 240 ordered pairs
-            secs = sum(big[k]["tiled_fused_us"] * (16 * 15 if k == "cnot" else 16) for k in
-                       ("depolarize", "x", "hadamard", "cnot")) * 1e-6
-            val = round(ops / secs, 2)
+            if big is not None and all("tiled_fused_us" in big[k] for k in ("depolarize", "x", "hadamard", "cnot")):
+                secs = sum(big[k]["tiled_fused_us"] * (16 * 15 if k == "cnot" else 16) for k in
+                           ("depolarize", "x", "hadamard", "cnot")) * 1e-6
+                val = round(ops / secs, 2)
+            else:
+                val = None   # a partial study (selected sizes / experiments) has no headline value
             cfg = {"workload": "the paper's experiments: depolarising p=0.1, X, Hadamard, CNOT over all positions, "
                                "n=6..16, packed column-major vs tiled (m=5) one op per pass vs tiled fused; value = "
                                "tiled fused ops/s over the four experiments at n=16 in df64"}

@@ -270,11 +270,36 @@ int orkan_sync(orkan_h h);
  * end only operation calls are allowed; blocking calls (measure, readouts,
  * init, sync) fail with EINVAL.  The handle needs a non-default stream (its
  * own, or one set with orkan_set_stream).  A graph is bound to the handle's
- * device memory and stays valid until orkan_graph_free. */
+ * device memory and stays valid until orkan_graph_free.  It replays physical
+ * passes: recording leaves the labels as they were at orkan_capture_begin;
+ * launching needs those labels (EINVAL otherwise) and leaves the labels the
+ * recorded calls ended with. */
 int orkan_capture_begin(orkan_h h);
 int orkan_capture_end(orkan_h h, void **graph);
 int orkan_graph_launch(orkan_h h, void *graph);
 int orkan_graph_free(void *graph);
+
+/* ------------------------------------------------------------------ qubit relabelling
+ * A handle keeps a map from logical qubits (the numbers every call takes and
+ * returns) to physical bit positions of the tiled layout, the identity after
+ * allocation and every init / load.  Relabelling moves data so that qubits a
+ * circuit uses often sit below the tile size m, where their ops run inside
+ * tiles and fuse freely, instead of spanning tile groups (Sec. III-C).  The
+ * operator a handle represents never changes: operations, measurements,
+ * Pauli expectations, elements and dense exports all translate through the
+ * map; orkan_expect relabels O to rho's map first; orkan_store_tiled and
+ * orkan_packed_from_tiled restore the identity map first (passes).  The
+ * allocation-free readout reads the physical layout as it is. */
+
+/* Set the map: phys[q] = physical position of logical qubit q (a permutation
+ * of 0..n-1).  Applied as at most n - 1 SWAP permutation passes (fused). */
+int orkan_relabel(orkan_h h, const int *phys);
+int orkan_get_labels(orkan_h h, int *phys);
+/* mode 1: orkan_run_circuit first gives the tile's m positions to the m
+ * qubits the circuit uses most, when the net number of ops that become
+ * in-tile (entering minus leaving) is at least four per swap it costs; the
+ * map then stays.  0 (default): never. */
+int orkan_set_relabel(orkan_h h, int mode);
 
 /* ------------------------------------------------------------------ packed column-major layout
  * Sec. III-A: the N (N + 1) / 2 lower-triangle elements column by column, h_ij

@@ -232,6 +232,9 @@ struct orkan_ctx {
   bool timing = false;
   bool capturing = false;
   double work_ops = 0.0, work_bytes = 0.0;   // algorithmic ALU ops / bytes of the timed passes
+  int phys[64];            // qubit relabelling: logical qubit -> physical bit position
+  int cap_phys[64];        // the map when the running graph capture began
+  int auto_relabel = 0;    // 1: orkan_run_circuit moves a circuit's most used qubits into the tile
   std::vector<cudaEvent_t> ev_free;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
 };
@@ -488,6 +491,25 @@ int check_qubits_n(int n, int k, const int* qubits) {
 }
 int check_qubits(const orkan_ctx* h, int k, const int* qubits) { return check_qubits_n(h->g.n, k, qubits); }
 
+// ------------------------------------------------------------------ qubit relabelling
+void reset_labels(orkan_ctx* h) {
+  for (int q = 0; q < 64; ++q) h->phys[q] = q;
+}
+bool labels_identity(const orkan_ctx* h) {
+  for (int q = 0; q < h->g.n; ++q)
+    if (h->phys[q] != q) return false;
+  return true;
+}
+// physical index of logical basis index l: bit q of l moves to bit phys[q]
+uint64_t phys_index(const orkan_ctx* h, uint64_t l) {
+  uint64_t p = 0;
+  for (int q = 0; q < h->g.n; ++q) p |= ((l >> q) & 1u) << h->phys[q];
+  return p;
+}
+void map_qubits(const orkan_ctx* h, int k, const int* q, int* out) {
+  for (int l = 0; l < k; ++l) out[l] = h->phys[q[l]];
+}
+
 // Build the planned op for a k-local Kraus set given in the caller's qubit order.
 // adj: build the adjoint map (observable handles).
 int make_op_adj(bool adj, int k, const int* qubits, const std::vector<Mat>& kraus_in, bool unitary, HostOp* out) {
@@ -594,6 +616,80 @@ HostOp make_ad_op(int q, const double R[16]) {
   return op;
 }
 
+// Move to the logical -> physical map tgt by swapping physical bit pairs (the
+// SWAP gate, a permutation pass), at most n - 1 swaps, fused by the planner.
+int relabel_to(orkan_ctx* h, const int* tgt) {
+  const int n = h->g.n;
+  int occ[64], want[64];
+  for (int q = 0; q < n; ++q) {
+    occ[h->phys[q]] = q;
+    want[tgt[q]] = q;
+  }
+  const Mat swap_gate = {1, 0, 0, 0, 0, 0, 1, 0, 0, 1, 0, 0, 0, 0, 0, 1};
+  for (int p = 0; p < n; ++p) {
+    if (occ[p] == want[p]) continue;
+    int r = p + 1;
+    while (occ[r] != want[p]) ++r;
+    const int pr[2] = {p, r};
+    HostOp op;
+    if (int st = make_op_adj(false, 2, pr, {swap_gate}, true, &op)) return st;
+    if (int st = enqueue(h, std::move(op))) return st;
+    std::swap(occ[p], occ[r]);
+  }
+  for (int q = 0; q < n; ++q) h->phys[q] = tgt[q];
+  return ORKAN_OK;
+}
+
+// Before a circuit: give the tile's m physical positions to the m logical
+// qubits the circuit uses most, when the net number of ops that become
+// in-tile (those that enter minus those that leave) is at least four per swap.  An incoming qubit swaps places with the least used
+// outgoing one; qubits already in the tile stay where they are.
+int plan_relabel(orkan_ctx* h, int count, const orkan_op* ops) {
+  const int n = h->g.n, m = h->g.m;
+  if (n <= m) return ORKAN_OK;
+  std::vector<int64_t> use(n, 0);
+  auto nq = [](const orkan_op& o) { return (o.kind == ORKAN_OP_UNITARY || o.kind == ORKAN_OP_KRAUS) ? o.k : 1; };
+  for (int i = 0; i < count; ++i)
+    for (int l = 0; l < nq(ops[i]) && l < 3; ++l)
+      if (ops[i].qubits[l] >= 0 && ops[i].qubits[l] < n) ++use[ops[i].qubits[l]];
+  std::vector<int> order(n);
+  for (int q = 0; q < n; ++q) order[q] = q;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return use[a] != use[b] ? use[a] > use[b] : h->phys[a] < h->phys[b];
+  });
+  std::vector<char> top(n, 0);
+  for (int i = 0; i < m; ++i)
+    if (use[order[i]] > 0) top[order[i]] = 1;
+  std::vector<int> in, out;
+  for (int i = 0; i < n; ++i) {
+    const int q = order[i];
+    if (top[q] && h->phys[q] >= m) in.push_back(q);
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    const int q = order[i];
+    if (!top[q] && h->phys[q] < m) out.push_back(q);
+  }
+  const size_t pairs = std::min(in.size(), out.size());
+  if (pairs == 0) return ORKAN_OK;
+  int tgt[64];
+  for (int q = 0; q < n; ++q) tgt[q] = h->phys[q];
+  for (size_t i = 0; i < pairs; ++i) std::swap(tgt[in[i]], tgt[out[i]]);
+  int64_t gain = 0;
+  for (int i = 0; i < count; ++i) {
+    bool low_now = true, low_then = true;
+    for (int l = 0; l < nq(ops[i]) && l < 3; ++l) {
+      const int q = ops[i].qubits[l];
+      if (q < 0 || q >= n) return ORKAN_OK;   // invalid op: leave the error to the op itself
+      low_now = low_now && h->phys[q] < m;
+      low_then = low_then && tgt[q] < m;
+    }
+    if (low_then && !low_now) ++gain;
+    if (low_now && !low_then) --gain;   // ops that would leave the tile count against
+  }
+  if (gain < 4 * int64_t(pairs)) return ORKAN_OK;
+  return relabel_to(h, tgt);
+}
+
 // Device staging space of at least `bytes` for host uploads, kept for the
 // handle's lifetime; earlier uploads are stream-ordered before later ones.
 int upload_space(orkan_ctx* h, size_t bytes, void** out) {
@@ -676,6 +772,7 @@ int common_alloc(int n, int dtype, int tile_log2, void* dev_ptr, size_t bytes, o
   if (!c) return fail(ORKAN_ENOMEM, "host allocation failed");
   c->g = g;
   c->dtype = dtype;
+  for (int q = 0; q < 64; ++q) c->phys[q] = c->cap_phys[q] = q;
   c->bytes = size_t(g.ntiles) << (2 * g.m);
   c->bytes *= elem_size(dtype);
   cudaGetDevice(&c->device);
@@ -703,6 +800,14 @@ int common_alloc(int n, int dtype, int tile_log2, void* dev_ptr, size_t bytes, o
 }  // namespace
 
 void orkan::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+// An instantiated circuit graph with the qubit labels it was recorded under.
+struct GraphRec {
+  cudaGraphExec_t exec = nullptr;
+  int n = 0;
+  int phys_begin[64];
+  int phys_end[64];
+};
 
 // =================================================================== C ABI
 extern "C" {
@@ -823,6 +928,7 @@ void* orkan_device_ptr(orkan_h h) { return h ? h->d_state : nullptr; }
 int orkan_init_state(orkan_h h, int kind, const double* data) {
   if (int st = check_blocking(h)) return st;
   h->pending.clear();
+  reset_labels(h);
   h->picture = ORKAN_STATE;
   switch (kind) {
     case ORKAN_INIT_ZERO:
@@ -885,6 +991,7 @@ int orkan_init_observable(orkan_h h, int nterms, const char* paulis, const doubl
   }
   std::stable_sort(terms.begin(), terms.end(), [](const Term& a, const Term& b) { return a.x < b.x; });
   h->pending.clear();
+  reset_labels(h);
   h->picture = ORKAN_OBSERVABLE;
   ORKAN_CUDA(launch_zero(h->dtype, h->d_state, h->g, h->stream));
   h->n_launches += 1;
@@ -913,6 +1020,7 @@ int orkan_load_tiled(orkan_h h, const void* host_src, int picture) {
   if (int st = check_blocking(h)) return st;
   if (!host_src || (picture != ORKAN_STATE && picture != ORKAN_OBSERVABLE)) return fail(ORKAN_EINVAL, "bad args");
   h->pending.clear();
+  reset_labels(h);
   h->picture = picture;
   ORKAN_CUDA(cudaMemcpyAsync(h->d_state, host_src, h->bytes, cudaMemcpyHostToDevice, h->stream));
   ORKAN_CUDA(cudaStreamSynchronize(h->stream));
@@ -922,6 +1030,11 @@ int orkan_load_tiled(orkan_h h, const void* host_src, int picture) {
 int orkan_store_tiled(orkan_h h, void* host_dst) {
   if (int st = check_blocking(h)) return st;
   if (!host_dst) return fail(ORKAN_EINVAL, "null destination");
+  if (!labels_identity(h)) {   // the stored layout is the logical one
+    int id[64];
+    for (int q = 0; q < 64; ++q) id[q] = q;
+    if (int st = relabel_to(h, id)) return st;
+  }
   if (int st = flush_pending(h)) return st;
   ORKAN_CUDA(cudaMemcpyAsync(host_dst, h->d_state, h->bytes, cudaMemcpyDeviceToHost, h->stream));
   ORKAN_CUDA(cudaStreamSynchronize(h->stream));
@@ -932,8 +1045,10 @@ int orkan_apply_unitary(orkan_h h, int k, const int* qubits, const double* U) {
   if (int st = check_handle(h)) return st;
   if (int st = check_qubits(h, k, qubits)) return st;
   if (!U) return fail(ORKAN_EINVAL, "null matrix");
+  int pq[3];
+  map_qubits(h, k, qubits, pq);
   HostOp op;
-  if (int st = make_op(h, k, qubits, {read_mat(U, 1 << k)}, true, &op)) return st;
+  if (int st = make_op(h, k, pq, {read_mat(U, 1 << k)}, true, &op)) return st;
   return enqueue(h, std::move(op));
 }
 
@@ -945,16 +1060,19 @@ int orkan_apply_kraus(orkan_h h, int k, const int* qubits, int r, const double* 
   const int d = 1 << k;
   std::vector<Mat> kraus;
   for (int a = 0; a < r; ++a) kraus.push_back(read_mat(K + 2 * d * d * a, d));
+  int pq[3];
+  map_qubits(h, k, qubits, pq);
   HostOp op;
-  if (int st = make_op(h, k, qubits, kraus, false, &op)) return st;
+  if (int st = make_op(h, k, pq, kraus, false, &op)) return st;
   return enqueue(h, std::move(op));
 }
 
 static int named_channel(orkan_h h, int q, const std::vector<Mat>& kraus) {
   if (int st = check_handle(h)) return st;
   if (int st = check_qubits(h, 1, &q)) return st;
+  const int pq = h->phys[q];
   HostOp op;
-  if (int st = make_op(h, 1, &q, kraus, false, &op)) return st;
+  if (int st = make_op(h, 1, &pq, kraus, false, &op)) return st;
   op.kind = OP_PTM1_AD;   // diagonal / amplitude-mixing structure holds exactly for these sets
   return enqueue(h, std::move(op));
 }
@@ -967,7 +1085,7 @@ int orkan_depolarize(orkan_h h, int q, double p) {
   // transfer matrix diag(1, f, f, f), f = 1 - 4p/3, used in closed form.
   const double f = 1.0 - 4.0 * p / 3.0;
   const double R[16] = {1, 0, 0, 0, 0, f, 0, 0, 0, 0, f, 0, 0, 0, 0, f};
-  return enqueue(h, make_ad_op(q, R));
+  return enqueue(h, make_ad_op(h->phys[q], R));
 }
 
 int orkan_dephase(orkan_h h, int q, double p) {
@@ -988,7 +1106,7 @@ int orkan_measure(orkan_h h, int q, double u, int* outcome, double* prob) {
   if (int st = check_qubits(h, 1, &q)) return st;
   if (!(u >= 0.0 && u < 1.0)) return fail(ORKAN_EINVAL, "u must be in [0, 1)");
   double r[4];
-  if (int st = reduce_diag(h, q, r)) return st;
+  if (int st = reduce_diag(h, h->phys[q], r)) return st;
   const double p0 = r[2], p1 = r[3], tot = p0 + p1;
   if (!(tot > 0.0)) return fail(ORKAN_EZEROPROB, "both outcomes have zero probability");
   const int b = (u * tot < p0) ? 0 : 1;
@@ -998,7 +1116,7 @@ int orkan_measure(orkan_h h, int q, double u, int* outcome, double* prob) {
   // transfer matrix of Pi_b . Pi_b / p_b
   const double sg = b ? -0.5 * s : 0.5 * s;
   const double R[16] = {0.5 * s, 0, 0, sg, 0, 0, 0, 0, 0, 0, 0, 0, sg, 0, 0, 0.5 * s};
-  if (int st = enqueue(h, make_ad_op(q, R))) return st;
+  if (int st = enqueue(h, make_ad_op(h->phys[q], R))) return st;
   if (outcome) *outcome = b;
   if (prob) *prob = pb / tot;
   return ORKAN_OK;
@@ -1010,7 +1128,7 @@ int orkan_project(orkan_h h, int q, int outcome) {
   if (outcome != 0 && outcome != 1) return fail(ORKAN_EINVAL, "outcome must be 0 or 1");
   const double sg = outcome ? -0.5 : 0.5;
   const double R[16] = {0.5, 0, 0, sg, 0, 0, 0, 0, 0, 0, 0, 0, sg, 0, 0, 0.5};
-  return enqueue(h, make_ad_op(q, R));
+  return enqueue(h, make_ad_op(h->phys[q], R));
 }
 
 // ------------------------------------------------------------------ packed column-major layout
@@ -1105,6 +1223,11 @@ int orkan_packed_depolarize(void* dev_packed, int n, int dtype, int q, double p,
 int orkan_packed_from_tiled(orkan_h h, void* dev_packed) {
   if (int st = check_handle(h)) return st;
   if (!dev_packed) return fail(ORKAN_EINVAL, "null packed array");
+  if (!labels_identity(h)) {
+    int id[64];
+    for (int q = 0; q < 64; ++q) id[q] = q;
+    if (int st = relabel_to(h, id)) return st;
+  }
   if (int st = flush_pending(h)) return st;
   ORKAN_CUDA(launch_packed_convert(h->dtype, dev_packed, h->d_state, h->g, 1, h->stream));
   return ORKAN_OK;
@@ -1114,6 +1237,7 @@ int orkan_packed_to_tiled(orkan_h h, const void* dev_packed) {
   if (int st = check_handle(h)) return st;
   if (!dev_packed) return fail(ORKAN_EINVAL, "null packed array");
   if (int st = flush_pending(h)) return st;
+  reset_labels(h);
   ORKAN_CUDA(launch_packed_convert(h->dtype, const_cast<void*>(dev_packed), h->d_state, h->g, 0, h->stream));
   return ORKAN_OK;
 }
@@ -1121,6 +1245,8 @@ int orkan_packed_to_tiled(orkan_h h, const void* dev_packed) {
 int orkan_run_circuit(orkan_h h, int count, const orkan_op* ops, int* outcomes, double* probs, int* done) {
   if (int st = check_handle(h)) return st;
   if (count < 0 || (count > 0 && !ops)) return fail(ORKAN_EINVAL, "bad op list");
+  if (h->auto_relabel)
+    if (int rst = plan_relabel(h, count, ops)) return rst;
   int nmeas = 0, i = 0, st = ORKAN_OK;
   for (; i < count && st == ORKAN_OK; ++i) {
     const orkan_op& o = ops[i];
@@ -1165,7 +1291,7 @@ int orkan_expect_pauli(orkan_h h, const char* pauli, double* out) {
   int ny = 0;
   for (int l = 0; l < h->g.n; ++l) {
     const char ch = pauli[l];
-    const uint64_t bit = uint64_t(1) << l;
+    const uint64_t bit = uint64_t(1) << h->phys[l];   // character l acts on logical qubit l
     if (ch == 'I') continue;
     if (ch == 'X') x |= bit;
     else if (ch == 'Y') { x |= bit; y |= bit; ++ny; }
@@ -1195,6 +1321,8 @@ int orkan_expect(orkan_h rho, orkan_h O, double* out) {
   if (!out) return fail(ORKAN_EINVAL, "null output");
   if (rho->g.n != O->g.n || rho->g.m != O->g.m || rho->dtype != O->dtype)
     return fail(ORKAN_EINVAL, "operands differ in n, tile size or dtype");
+  if (O != rho && !std::equal(rho->phys, rho->phys + rho->g.n, O->phys))
+    if (int st = relabel_to(O, rho->phys)) return st;   // same physical layout for the tile-wise products
   if (int st = flush_pending(O)) return st;
   if (O != rho) ORKAN_CUDA(cudaStreamSynchronize(O->stream));
   if (int st = flush_pending(rho)) return st;
@@ -1217,11 +1345,25 @@ int orkan_to_dense(orkan_h h, double* out) {
     cudaGetLastError();
     return fail(ORKAN_ENOMEM, "cudaMalloc(dense) failed");
   }
+  const bool ident = labels_identity(h);
+  std::vector<double> phys_dense;
+  if (!ident) phys_dense.resize(size_t(h->g.N) * size_t(h->g.N) * 2);
   cudaError_t e = launch_to_dense(h->dtype, h->d_state, h->g, tmp, h->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ident ? out : phys_dense.data(), tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(tmp);
   if (e != cudaSuccess) return cuda_fail(e, "to_dense");
+  if (!ident) {   // logical (i, j) sits at the physical indices of its bits
+    const int64_t N = h->g.N;
+    std::vector<int64_t> pi(N);
+    for (int64_t i = 0; i < N; ++i) pi[i] = int64_t(phys_index(h, uint64_t(i)));
+    for (int64_t i = 0; i < N; ++i)
+      for (int64_t j = 0; j < N; ++j) {
+        const size_t src = (size_t(pi[i]) * N + size_t(pi[j])) * 2, dst = (size_t(i) * N + size_t(j)) * 2;
+        out[dst] = phys_dense[src];
+        out[dst + 1] = phys_dense[src + 1];
+      }
+  }
   h->n_launches += 1;
   return ORKAN_OK;
 }
@@ -1234,6 +1376,17 @@ int orkan_get_elements(orkan_h h, int64_t count, const int64_t* rows, const int6
     if (rows[t] < 0 || rows[t] >= h->g.N || cols[t] < 0 || cols[t] >= h->g.N)
       return fail(ORKAN_EINVAL, "element index out of range");
   if (int st = flush_pending(h)) return st;
+  std::vector<int64_t> prow, pcol;
+  if (!labels_identity(h)) {
+    prow.resize(count);
+    pcol.resize(count);
+    for (int64_t t = 0; t < count; ++t) {
+      prow[t] = int64_t(phys_index(h, uint64_t(rows[t])));
+      pcol[t] = int64_t(phys_index(h, uint64_t(cols[t])));
+    }
+    rows = prow.data();
+    cols = pcol.data();
+  }
   int64_t* d_idx = nullptr;
   double* d_out = nullptr;
   if (cudaMalloc(&d_idx, size_t(count) * 16) != cudaSuccess || cudaMalloc(&d_out, size_t(count) * 16) != cudaSuccess) {
@@ -1271,6 +1424,7 @@ int orkan_capture_begin(orkan_h h) {
   if (int st = flush_pending(h)) return st;
   ORKAN_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   h->capturing = true;
+  std::copy(h->phys, h->phys + 64, h->cap_phys);
   return ORKAN_OK;
 }
 
@@ -1281,6 +1435,10 @@ int orkan_capture_end(orkan_h h, void** graph) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->stream, &g);
   h->capturing = false;
+  // nothing ran: the data still has the labels the capture began with
+  int end_phys[64];
+  std::copy(h->phys, h->phys + 64, end_phys);
+  std::copy(h->cap_phys, h->cap_phys + 64, h->phys);
   if (fst != ORKAN_OK) {
     if (g) cudaGraphDestroy(g);
     return fst;
@@ -1290,21 +1448,66 @@ int orkan_capture_end(orkan_h h, void** graph) {
   e = cudaGraphInstantiate(&ex, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-  *graph = ex;
+  GraphRec* rec = new (std::nothrow) GraphRec;
+  if (!rec) {
+    cudaGraphExecDestroy(ex);
+    return fail(ORKAN_ENOMEM, "host allocation failed");
+  }
+  rec->exec = ex;
+  rec->n = h->g.n;
+  std::copy(h->cap_phys, h->cap_phys + 64, rec->phys_begin);
+  std::copy(end_phys, end_phys + 64, rec->phys_end);
+  *graph = rec;
   return ORKAN_OK;
 }
 
 int orkan_graph_launch(orkan_h h, void* graph) {
   if (int st = check_blocking(h)) return st;
   if (!graph) return fail(ORKAN_EINVAL, "null graph");
+  const GraphRec* rec = static_cast<const GraphRec*>(graph);
+  // the recorded passes act on physical qubits: the labels must be those the capture began with
+  if (rec->n != h->g.n || !std::equal(rec->phys_begin, rec->phys_begin + rec->n, h->phys))
+    return fail(ORKAN_EINVAL, "the handle's qubit labels differ from those when the graph was captured");
   if (int st = flush_pending(h)) return st;
-  ORKAN_CUDA(cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph), h->stream));
+  ORKAN_CUDA(cudaGraphLaunch(rec->exec, h->stream));
+  std::copy(rec->phys_end, rec->phys_end + 64, h->phys);
   h->n_launches += 1;
   return ORKAN_OK;
 }
 
 int orkan_graph_free(void* graph) {
-  if (graph) ORKAN_CUDA(cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(graph)));
+  if (!graph) return ORKAN_OK;
+  GraphRec* rec = static_cast<GraphRec*>(graph);
+  const cudaError_t e = cudaGraphExecDestroy(rec->exec);
+  delete rec;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphExecDestroy");
+  return ORKAN_OK;
+}
+
+int orkan_relabel(orkan_h h, const int* phys) {
+  if (int st = check_handle(h)) return st;
+  if (!phys) return fail(ORKAN_EINVAL, "null map");
+  std::vector<char> seen(h->g.n, 0);
+  for (int q = 0; q < h->g.n; ++q) {
+    if (phys[q] < 0 || phys[q] >= h->g.n || seen[phys[q]]) return fail(ORKAN_EINVAL, "map must be a permutation of 0..n-1");
+    seen[phys[q]] = 1;
+  }
+  int tgt[64];
+  for (int q = 0; q < 64; ++q) tgt[q] = q < h->g.n ? phys[q] : q;
+  return relabel_to(h, tgt);
+}
+
+int orkan_get_labels(orkan_h h, int* phys) {
+  if (int st = check_handle(h)) return st;
+  if (!phys) return fail(ORKAN_EINVAL, "null output");
+  std::copy(h->phys, h->phys + h->g.n, phys);
+  return ORKAN_OK;
+}
+
+int orkan_set_relabel(orkan_h h, int mode) {
+  if (int st = check_handle(h)) return st;
+  if (mode != 0 && mode != 1) return fail(ORKAN_EINVAL, "mode must be 0 or 1");
+  h->auto_relabel = mode;
   return ORKAN_OK;
 }
 

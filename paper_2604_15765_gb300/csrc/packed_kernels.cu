@@ -45,7 +45,9 @@ __device__ __forceinline__ void pk_write(typename P::Elem* st, int64_t i, int64_
   st[pk_col(q, N) + (p - q)] = P::conj_if(P::make(v.re, v.im), cj ? 1u : 0u);
 }
 
-template <class P, int K>
+// One kernel per (policy, k, op form): the form is a compile-time constant, so
+// no other form's arithmetic is ever issued.
+template <class P, int K, int FORM>
 __global__ void __launch_bounds__(kPkThreads) k_packed_op(typename P::Elem* __restrict__ st,
                                                           const __grid_constant__ PackedDesc d) {
   constexpr int B = 1 << K;
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(kPkThreads) k_packed_op(typename P::Elem* __re
     }
     Cx<P> h[B * B];
     const double* cf = d.coef;
-    if (d.kind == OP_MONO1 || d.kind == OP_MONO2) {
+    if constexpr (FORM == OP_MONO1 || FORM == OP_MONO2) {
       // V[x][p_x] = i^{q_x}: (V h V^dagger)[x][y] = i^{q_x - q_y} h[p_x][p_y],
       // gathered in permuted order straight from memory (no arithmetic)
       const int cb = K == 1 ? 0 : 32;
@@ -84,15 +86,10 @@ __global__ void __launch_bounds__(kPkThreads) k_packed_op(typename P::Elem* __re
       for (int x = 0; x < B; ++x)
 #pragma unroll
         for (int y = 0; y < B; ++y) h[x * B + y] = pk_read<P>(st, ib | dep(x), jb | dep(y), N);
-      if constexpr (K == 1) {
-        switch (d.kind) {
-          case OP_PTM1_U: body_ptm1_u<P>(h[0], h[1], h[2], h[3], cf); break;
-          case OP_PTM1_AD: body_ptm1_ad<P>(h[0], h[1], h[2], h[3], cf); break;
-          default: body_ptm1<P>(h[0], h[1], h[2], h[3], cf); break;
-        }
-      } else {
-        body_u2<P>(h, cf);
-      }
+      if constexpr (FORM == OP_PTM1_U) body_ptm1_u<P>(h[0], h[1], h[2], h[3], cf);
+      else if constexpr (FORM == OP_PTM1_AD) body_ptm1_ad<P>(h[0], h[1], h[2], h[3], cf);
+      else if constexpr (FORM == OP_PTM1) body_ptm1<P>(h[0], h[1], h[2], h[3], cf);
+      else body_u2<P>(h, cf);
     }
     const bool dblk = s == sp;
 #pragma unroll
@@ -141,8 +138,16 @@ int grid_for(int64_t work) {
 template <class P>
 cudaError_t launch_packed_t(void* state, const PackedDesc& d, cudaStream_t s) {
   auto* st = reinterpret_cast<typename P::Elem*>(state);
-  if (d.k == 1) k_packed_op<P, 1><<<grid_for(d.n_blocks), kPkThreads, 0, s>>>(st, d);
-  else k_packed_op<P, 2><<<grid_for(d.n_blocks), kPkThreads, 0, s>>>(st, d);
+  const int grid = grid_for(d.n_blocks);
+  switch (d.kind) {
+    case OP_PTM1: k_packed_op<P, 1, OP_PTM1><<<grid, kPkThreads, 0, s>>>(st, d); break;
+    case OP_PTM1_U: k_packed_op<P, 1, OP_PTM1_U><<<grid, kPkThreads, 0, s>>>(st, d); break;
+    case OP_PTM1_AD: k_packed_op<P, 1, OP_PTM1_AD><<<grid, kPkThreads, 0, s>>>(st, d); break;
+    case OP_MONO1: k_packed_op<P, 1, OP_MONO1><<<grid, kPkThreads, 0, s>>>(st, d); break;
+    case OP_U2: k_packed_op<P, 2, OP_U2><<<grid, kPkThreads, 0, s>>>(st, d); break;
+    case OP_MONO2: k_packed_op<P, 2, OP_MONO2><<<grid, kPkThreads, 0, s>>>(st, d); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -94,6 +94,9 @@ _SIGS = {
     "orkan_pass_work": (C.c_int, [_h, _pd, _pd]),
     "orkan_expect_paulis_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_char_p, _pd,
                                               C.c_void_p]),
+    "orkan_relabel": (C.c_int, [_h, _pi]),
+    "orkan_get_labels": (C.c_int, [_h, _pi]),
+    "orkan_set_relabel": (C.c_int, [_h, C.c_int]),
     "orkan_packed_bytes": (C.c_size_t, [C.c_int, C.c_int]),
     "orkan_packed_offset": (_i64, [C.c_int, _i64, _i64, _pi]),
     "orkan_packed_apply_unitary": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, _pi, _pd, C.c_void_p]),
@@ -367,6 +370,21 @@ def orkan_expect_paulis_noalloc(dev_state: int, n: int, dtype: int, tile_log2: i
     _check(_lib.orkan_expect_paulis_noalloc(C.c_void_p(dev_state), n, dtype, tile_log2, len(paulis), s, _dptr(out),
                                             C.c_void_p(stream_ptr or 0)), "orkan_expect_paulis_noalloc")
     return out
+
+
+# ------------------------------------------------------------------ qubit relabelling
+def orkan_relabel(h, phys):
+    _check(_lib.orkan_relabel(h, _qubits(phys)), "orkan_relabel")
+
+
+def orkan_get_labels(h, n: int):
+    arr = (C.c_int * n)()
+    _check(_lib.orkan_get_labels(h, arr), "orkan_get_labels")
+    return list(arr)
+
+
+def orkan_set_relabel(h, mode: int):
+    _check(_lib.orkan_set_relabel(h, mode), "orkan_set_relabel")
 
 
 # ------------------------------------------------------------------ packed column-major layout
