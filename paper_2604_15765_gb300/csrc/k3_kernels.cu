@@ -121,7 +121,8 @@ __device__ __forceinline__ void k3_term(const Cx<P> (&h)[8], Cx<P> (&acc)[8], ty
   }
 }
 
-template <class P>
+// MONO: the monomial form (compile-time, so the Kraus sweep carries no codes).
+template <class P, bool MONO>
 __global__ void __launch_bounds__(kK3Threads) k3_kernel(typename P::Elem* __restrict__ st,
                                                         const __grid_constant__ K3Desc d) {
   using E = typename P::Elem;
@@ -136,44 +137,57 @@ __global__ void __launch_bounds__(kK3Threads) k3_kernel(typename P::Elem* __rest
   auto dep = [&](int x) -> uint64_t {
     return (uint64_t(x & 1) << q0) | (uint64_t((x >> 1) & 1) << q1) | (uint64_t((x >> 2) & 1) << q2);
   };
+  // monomial codes in registers once, outside the loop (p: source index, q: phase)
+  int pc[8] = {}, qc[8] = {};
+  if constexpr (MONO) {
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      pc[x] = icoef(d.coef, x);
+      qc[x] = icoef(d.coef, 8 + x);
+    }
+  }
   for (int64_t b = int64_t(blockIdx.x) * kK3Blocks + lb; b < d.nblocks; b += int64_t(gridDim.x) * kK3Blocks) {
     const int64_t s = tri_row(b), sp = b - s * (s + 1) / 2;
     const uint64_t ib = uint64_t(ins0(ins0(ins0(s, q0), q1), q2));
     const uint64_t jb = uint64_t(ins0(ins0(ins0(sp, q0), q1), q2));
     const bool dblk = s == sp;   // a hermitian block: only x >= y is written
 
-    if (d.form == 1) {
+    if constexpr (MONO) {
       // (L h L^dagger)[a][c] = i^{q_a - q_c} h[p_a][p_c]
-      const int pa = icoef(d.coef, a), qa = icoef(d.coef, 8 + a);
+      int pa = pc[0], qa = qc[0];
+#pragma unroll
+      for (int x = 1; x < 8; ++x)
+        if (a == x) {
+          pa = pc[x];
+          qa = qc[x];
+        }
       const uint64_t isrc = ib | dep(pa);
       Cx<P> v[8];
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
-        v[c] = rot_i<P>(k3_read<P>(st, isrc, jb | dep(icoef(d.coef, c)), m), qa - icoef(d.coef, 8 + c));
+      for (int c = 0; c < 8; ++c) v[c] = rot_i<P>(k3_read<P>(st, isrc, jb | dep(pc[c]), m), qa - qc[c]);
       __syncwarp(mask);   // every read of the block precedes every write
       const uint64_t i = ib | dep(a);
 #pragma unroll
       for (int c = 0; c < 8; ++c)
         if (!dblk || a >= c) k3_write<P>(st, i, jb | dep(c), m, v[c]);
-      continue;
-    }
-
-    Cx<P> h[8];
-    {
-      const uint64_t i = ib | dep(a);
+    } else {
+      Cx<P> h[8];
+      {
+        const uint64_t i = ib | dep(a);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) h[c] = k3_read<P>(st, i, jb | dep(c), m);
-    }
-    Cx<P> acc[8];
-    // the first term with compile-time coefficient offsets (the whole of a
-    // unitary), further Kraus terms in a loop
-    k3_term<P, true>(h, acc, ybuf[lb], d.coef, a, mask);
+        for (int c = 0; c < 8; ++c) h[c] = k3_read<P>(st, i, jb | dep(c), m);
+      }
+      Cx<P> acc[8];
+      // the first term with compile-time coefficient offsets (the whole of a
+      // unitary), further Kraus terms in a loop
+      k3_term<P, true>(h, acc, ybuf[lb], d.coef, a, mask);
 #pragma unroll 1
-    for (int t = 1; t < d.r; ++t) k3_term<P, false>(h, acc, ybuf[lb], d.coef + 128 * t, a, mask);
-    const uint64_t j = jb | dep(a);
+      for (int t = 1; t < d.r; ++t) k3_term<P, false>(h, acc, ybuf[lb], d.coef + 128 * t, a, mask);
+      const uint64_t j = jb | dep(a);
 #pragma unroll
-    for (int x = 0; x < 8; ++x)
-      if (!dblk || x >= a) k3_write<P>(st, ib | dep(x), j, m, acc[x]);
+      for (int x = 0; x < 8; ++x)
+        if (!dblk || x >= a) k3_write<P>(st, ib | dep(x), j, m, acc[x]);
+    }
   }
 }
 
@@ -185,7 +199,8 @@ cudaError_t launch_k3_t(void* state, const K3Desc& d, cudaStream_t s) {
   if (err != cudaSuccess) return err;
   const int64_t need = (d.nblocks + kK3Blocks - 1) / kK3Blocks;
   const int ctas = int(std::min<int64_t>(need, int64_t(sms) * 8));
-  k3_kernel<P><<<ctas, kK3Threads, 0, s>>>(reinterpret_cast<typename P::Elem*>(state), d);
+  if (d.form == 1) k3_kernel<P, true><<<ctas, kK3Threads, 0, s>>>(reinterpret_cast<typename P::Elem*>(state), d);
+  else k3_kernel<P, false><<<ctas, kK3Threads, 0, s>>>(reinterpret_cast<typename P::Elem*>(state), d);
   return cudaGetLastError();
 }
 

@@ -57,6 +57,16 @@ __global__ void __launch_bounds__(kPkThreads) k_packed_op(typename P::Elem* __re
   auto dep = [&](int x) -> int64_t {
     return K == 1 ? int64_t(x) << q0 : (int64_t(x & 1) << q0) | (int64_t(x >> 1) << q1);
   };
+  // monomial codes in registers once, outside the loop (p: source index, q: phase)
+  int pc[B] = {}, qc[B] = {};
+  if constexpr (FORM == OP_MONO1 || FORM == OP_MONO2) {
+    constexpr int cb = K == 1 ? 0 : 32;
+#pragma unroll
+    for (int x = 0; x < B; ++x) {
+      pc[x] = icoef(d.coef, cb + x);
+      qc[x] = icoef(d.coef, cb + B + x);
+    }
+  }
   for (int64_t g = int64_t(blockIdx.x) * kPkThreads + threadIdx.x; g < d.n_blocks;
        g += int64_t(gridDim.x) * kPkThreads) {
     // g -> (column block sp, row block s >= sp): columns from the last one
@@ -74,13 +84,11 @@ __global__ void __launch_bounds__(kPkThreads) k_packed_op(typename P::Elem* __re
     if constexpr (FORM == OP_MONO1 || FORM == OP_MONO2) {
       // V[x][p_x] = i^{q_x}: (V h V^dagger)[x][y] = i^{q_x - q_y} h[p_x][p_y],
       // gathered in permuted order straight from memory (no arithmetic)
-      const int cb = K == 1 ? 0 : 32;
 #pragma unroll
       for (int x = 0; x < B; ++x)
 #pragma unroll
         for (int y = 0; y < B; ++y)
-          h[x * B + y] = rot_i<P>(pk_read<P>(st, ib | dep(icoef(cf, cb + x)), jb | dep(icoef(cf, cb + y)), N),
-                                  icoef(cf, cb + B + x) - icoef(cf, cb + B + y));
+          h[x * B + y] = rot_i<P>(pk_read<P>(st, ib | dep(pc[x]), jb | dep(pc[y]), N), qc[x] - qc[y]);
     } else {
 #pragma unroll
       for (int x = 0; x < B; ++x)

@@ -498,9 +498,10 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------ the pass kernel
-// Persistent CTAs walk the work items with a two-stage shared-memory
-// pipeline: the 16-byte asynchronous copies of item i + 1 are in flight while
-// item i is transformed and written back, so HBM reads overlap the arithmetic.
+// Persistent CTAs walk the work items with a three-buffer shared-memory
+// pipeline: the 16-byte asynchronous copies of items i + 1 and i + 2 are in
+// flight while item i is transformed and written back, so HBM reads overlap
+// the arithmetic and two items' worth of reads cover the memory latency.
 constexpr int kMainThreads = 512;
 
 // PACK: an in-tile pass (no high qubit) runs on the H = 1 geometry with four
@@ -518,11 +519,11 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
   constexpr int RL = rows_log2_ct(H, MLOG, int(sizeof(E)));
   using G = GMap<P, H, MLOG, RL>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // per-item slot info, three items deep: item i+2 is decoded while item i+1
-  // loads and item i computes
-  __shared__ int64_t s_base[3][NSLOT];
-  __shared__ unsigned s_tmask[3], s_vmask[3];
-  __shared__ int s_diag[3];
+  // per-item slot info, four items deep: item i computes, items i+1 and i+2
+  // load, item i+3 is decoded
+  __shared__ int64_t s_base[4][NSLOT];
+  __shared__ unsigned s_tmask[4], s_vmask[4];
+  __shared__ int s_diag[4];
   E* bufs = reinterpret_cast<E*>(smem_raw);
   constexpr int m = MLOG, M = 1 << MLOG;
   constexpr int rl = RL, R = 1 << RL;
@@ -607,28 +608,30 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
     }
   };
 
-  // Three stages: item i computes in buffer i % 3 while the copies of item
-  // i + 1 fill buffer (i + 1) % 3; the slot info of item i + 2 is decoded
-  // meanwhile and made visible to all threads by the op barriers.
+  // Three stages, two items of copies in flight: item i computes in buffer
+  // i % 3 while the copies of items i + 1 and i + 2 fill the other two.  The
+  // copies of item i + 2 are issued after the barrier that ends item i - 1,
+  // whose buffer they reuse; slot info runs one item further ahead (item i + 3
+  // is decoded meanwhile and made visible by the barriers that follow).
   const int64_t G0 = gridDim.x;
   int64_t w = blockIdx.x;
-  if (w < d.n_items) item_info(w, 0);
-  if (w + G0 < d.n_items) item_info(w + G0, 1);
+  for (int k = 0; k < 3; ++k)
+    if (w + k * G0 < d.n_items) item_info(w + k * G0, k);
   __syncthreads();
-  if (w < d.n_items) issue_loads(w, 0, bufs);
-  cp_async_commit();
-  for (int it = 0; w < d.n_items; ++it, w += G0) {
-    const int ic = it % 3, in1 = (it + 1) % 3, in2 = (it + 2) % 3;
-    E* sm = bufs + ic * buf_elems;
-    // buffer (it + 1) % 3 was last read by item it - 2, finished before the
-    // previous iteration's barrier
-    if (w + G0 < d.n_items) issue_loads(w + G0, in1, bufs + in1 * buf_elems);
+  for (int k = 0; k < 2; ++k) {
+    if (w + k * G0 < d.n_items) issue_loads(w + k * G0, k, bufs + k * buf_elems);
     cp_async_commit();
-    cp_async_wait_prev();
-    __syncthreads();
-    if (w + 2 * G0 < d.n_items) item_info(w + 2 * G0, in2);
+  }
+  for (int it = 0; w < d.n_items; ++it, w += G0) {
+    const int ic = it % 3, ii = it & 3;
+    E* sm = bufs + ic * buf_elems;
+    cp_async_wait_prev();   // the copies of item it are done (item it + 1 may still be in flight)
+    __syncthreads();        // ... and visible; every thread is past item it - 1
+    if (w + 2 * G0 < d.n_items) issue_loads(w + 2 * G0, (it + 2) & 3, bufs + ((it + 2) % 3) * buf_elems);
+    cp_async_commit();
+    if (w + 3 * G0 < d.n_items) item_info(w + 3 * G0, (it + 3) & 3);
 
-    const unsigned tm = s_tmask[ic], vm = s_vmask[ic];
+    const unsigned tm = s_tmask[ii], vm = s_vmask[ii];
     if (tm) {   // upper slots arrive transposed but not yet conjugated
 #pragma unroll 1
       for (int slot = 0; slot < NSLOT; ++slot) {
@@ -654,11 +657,11 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
     // granules, upper slots conjugated into their stored partner (skipped in
     // a diagonal group, where they mirror lower slots of the same group)
     const int r0 = int(w & chunk_mask) << rl;
-    const bool diag = s_diag[ic];
+    const bool diag = s_diag[ii];
 #pragma unroll 1
     for (int slot = 0; slot < NSLOT; ++slot) {
       if (!((vm >> slot) & 1u)) continue;
-      E* gbase = st + s_base[ic][slot];
+      E* gbase = st + s_base[ii][slot];
       const E* sbuf = sm + (slot << slot_log2);
       if (!((tm >> slot) & 1u)) {
         constexpr int NG = 1 << (slot_log2 - GSH);
