@@ -24,7 +24,6 @@ struct PolF64 {
   using Coef = double;
   static constexpr int kSwizzle = 7;  // 16-byte elements: 8 per 128-byte bank line
   static constexpr int kSwShift = 0;  // swizzle granule = 1 element (16 B)
-  static constexpr int kOpUnroll = 2;  // blocks per thread unrolled in the op loops
   static __device__ __forceinline__ Coef coef(const double* c, int i) { return c[i]; }
   // conjugate when t == 1, by flipping the sign bit (no FP64 instruction)
   static __device__ __forceinline__ Elem conj_if(Elem e, unsigned t) {
@@ -56,7 +55,6 @@ struct PolF32 {
   using Coef = float;
   static constexpr int kSwizzle = 15;  // 8-byte elements: 16 per 128-byte bank line
   static constexpr int kSwShift = 1;   // swizzle granule = 2 elements (16 B, one cp.async)
-  static constexpr int kOpUnroll = 4;
   static __device__ __forceinline__ Coef coef(const double* c, int i) {
     return reinterpret_cast<const float*>(c)[2 * i];
   }
@@ -105,7 +103,6 @@ struct PolDF64 {
   using Coef = float2;   // (hi, lo) split of an FP64 coefficient, made on the host
   static constexpr int kSwizzle = 7;
   static constexpr int kSwShift = 0;
-  static constexpr int kOpUnroll = 2;   // two blocks in flight per thread
   static __device__ __forceinline__ Coef coef(const double* c, int i) {
     return reinterpret_cast<const float2*>(c)[i];
   }

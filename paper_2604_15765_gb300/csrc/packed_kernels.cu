@@ -81,9 +81,24 @@ __global__ void __launch_bounds__(kPkThreads) k_packed_op(typename P::Elem* __re
     }
     Cx<P> h[B * B];
     const double* cf = d.coef;
-    if constexpr (FORM == OP_MONO1 || FORM == OP_MONO2) {
-      // V[x][p_x] = i^{q_x}: (V h V^dagger)[x][y] = i^{q_x - q_y} h[p_x][p_y],
-      // gathered in permuted order straight from memory (no arithmetic)
+    if constexpr (FORM == OP_MONO1) {
+      // V[x][p_x] = i^{q_x}: (V h V^dagger)[x][y] = i^{q_x - q_y} h[p_x][p_y];
+      // the block is read in its natural order and permuted in registers
+      Cx<P> v[4];
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) v[x * 2 + y] = pk_read<P>(st, ib | dep(x), jb | dep(y), N);
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+          const int t = pc[x] * 2 + pc[y];
+          const Cx<P> z = t == 0 ? v[0] : (t == 1 ? v[1] : (t == 2 ? v[2] : v[3]));
+          h[x * 2 + y] = rot_i<P>(z, qc[x] - qc[y]);
+        }
+    } else if constexpr (FORM == OP_MONO2) {
+      // the same permutation for 4x4 blocks, gathered in permuted order
 #pragma unroll
       for (int x = 0; x < B; ++x)
 #pragma unroll

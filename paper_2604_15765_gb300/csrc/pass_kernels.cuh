@@ -351,30 +351,60 @@ __device__ __forceinline__ void matvec4_mono(const Cx<P> (&in)[4], Cx<P> (&out)[
 }
 
 // ------------------------------------------------------------------ op drivers
-template <class P, class G, int NT, int rows_log2g, int cols_log2g>
-__device__ __forceinline__ void apply_1q(typename P::Elem* sm, const G& gm, const PassOp& op, const double* coef) {
+// Every driver walks its units with a compile-time count per thread (the
+// unit count is a power of two fixed by the geometry), and is instantiated
+// per op form, so the element loops carry no bounds or form branches.
+// ROLLED keeps the unit loop rolled (the kernels that also hold the large
+// generic two-qubit body, where unrolling would spill).
+template <int ITERS, bool ROLLED, class F>
+__device__ __forceinline__ void for_units(F&& unit) {
+  if constexpr (ROLLED) {
+#pragma unroll 1
+    for (int k = 0; k < ITERS; ++k) unit(k);
+  } else {
+#pragma unroll
+    for (int k = 0; k < ITERS; ++k) unit(k);
+  }
+}
+
+template <class P, class G, int NT, int rows_log2g, int cols_log2g, bool ROLLED, int FORM>
+__device__ __forceinline__ void apply_1q_form(typename P::Elem* sm, const G& gm, const PassOp& op,
+                                              const double* cf) {
   constexpr int ncb_log2 = cols_log2g - 1;
   constexpr int nb = 1 << (rows_log2g - 1 + ncb_log2);
+  constexpr int iters = (nb + NT - 1) / NT;
   int ra, rx, ca, cx;
   gm.row_delta(op.rbit[0], ra, rx);
   gm.col_delta(op.cbit[0], ca, cx);
+  for_units<iters, ROLLED>([&](int k) {
+    const int b = int(threadIdx.x) + k * NT;
+    if (nb % NT == 0 || b < nb) {
+      const int c0 = ins0i(b & ((1 << ncb_log2) - 1), op.cbit[0]);
+      const int r0 = ins0i(b >> ncb_log2, op.rbit[0]);
+      const int i00 = gm.idx(r0, c0);
+      const int i01 = (i00 + ca) ^ cx, i10 = (i00 + ra) ^ rx;
+      const int i11 = (i10 + ca) ^ cx;
+      Cx<P> a = ld<P>(sm, i00), bb = ld<P>(sm, i01), c = ld<P>(sm, i10), d = ld<P>(sm, i11);
+      if constexpr (FORM == OP_PTM1_U) body_ptm1_u<P>(a, bb, c, d, cf);
+      else if constexpr (FORM == OP_PTM1_AD) body_ptm1_ad<P>(a, bb, c, d, cf);
+      else if constexpr (FORM == OP_MONO1) body_mono1<P>(a, bb, c, d, cf);
+      else body_ptm1<P>(a, bb, c, d, cf);
+      st<P>(sm, i00, a);
+      st<P>(sm, i01, bb);
+      st<P>(sm, i10, c);
+      st<P>(sm, i11, d);
+    }
+  });
+}
+
+template <class P, class G, int NT, int rows_log2g, int cols_log2g, bool ROLLED = false>
+__device__ __forceinline__ void apply_1q(typename P::Elem* sm, const G& gm, const PassOp& op, const double* coef) {
   const double* cf = coef + op.coef;
-#pragma unroll(P::kOpUnroll)
-  for (int b = threadIdx.x; b < nb; b += NT) {
-    const int c0 = ins0i(b & ((1 << ncb_log2) - 1), op.cbit[0]);
-    const int r0 = ins0i(b >> ncb_log2, op.rbit[0]);
-    const int i00 = gm.idx(r0, c0);
-    const int i01 = (i00 + ca) ^ cx, i10 = (i00 + ra) ^ rx;
-    const int i11 = (i10 + ca) ^ cx;
-    Cx<P> a = ld<P>(sm, i00), bb = ld<P>(sm, i01), c = ld<P>(sm, i10), d = ld<P>(sm, i11);
-    if (op.kind == OP_PTM1_U) body_ptm1_u<P>(a, bb, c, d, cf);
-    else if (op.kind == OP_PTM1_AD) body_ptm1_ad<P>(a, bb, c, d, cf);
-    else if (op.kind == OP_MONO1) body_mono1<P>(a, bb, c, d, cf);
-    else body_ptm1<P>(a, bb, c, d, cf);
-    st<P>(sm, i00, a);
-    st<P>(sm, i01, bb);
-    st<P>(sm, i10, c);
-    st<P>(sm, i11, d);
+  switch (op.kind) {
+    case OP_PTM1_U: apply_1q_form<P, G, NT, rows_log2g, cols_log2g, ROLLED, OP_PTM1_U>(sm, gm, op, cf); break;
+    case OP_PTM1_AD: apply_1q_form<P, G, NT, rows_log2g, cols_log2g, ROLLED, OP_PTM1_AD>(sm, gm, op, cf); break;
+    case OP_MONO1: apply_1q_form<P, G, NT, rows_log2g, cols_log2g, ROLLED, OP_MONO1>(sm, gm, op, cf); break;
+    default: apply_1q_form<P, G, NT, rows_log2g, cols_log2g, ROLLED, OP_PTM1>(sm, gm, op, cf); break;
   }
 }
 
@@ -382,33 +412,35 @@ __device__ __forceinline__ void apply_1q(typename P::Elem* sm, const G& gm, cons
 // every row gets h[r, :] <- h[r, :] V^dagger on the column bits, then every
 // column gets h[:, c] <- V h[:, c] on the row bits.  Same 32 multiply-adds per
 // element as the block form, in 4-element units (small code, few registers).
-template <class P, class G, int NT, int rows_log2g, int cols_log2g>
-__device__ __forceinline__ void apply_u2_sep(typename P::Elem* sm, const G& gm, const PassOp& op,
-                                             const double* coef) {
-  const double* cf = coef + op.coef;
+template <class P, class G, int NT, int rows_log2g, int cols_log2g, bool ROLLED, bool MONO>
+__device__ __forceinline__ void apply_u2_sep_form(typename P::Elem* sm, const G& gm, const PassOp& op,
+                                                  const double* cf) {
   {
     int a0, x0, a1, x1;
     gm.col_delta(op.cbit[0], a0, x0);
     gm.col_delta(op.cbit[1], a1, x1);
     constexpr int nc_log2 = cols_log2g - 2;
     constexpr int nu = 1 << (rows_log2g + nc_log2);
-#pragma unroll(P::kOpUnroll)
-    for (int u = threadIdx.x; u < nu; u += NT) {
-      const int li = u >> nc_log2;
-      const int c0 = ins0i(ins0i(u & ((1 << nc_log2) - 1), op.cbit[0]), op.cbit[1]);
-      int ix[4];
-      ix[0] = gm.idx(li, c0);
-      ix[1] = (ix[0] + a0) ^ x0;
-      ix[2] = (ix[0] + a1) ^ x1;
-      ix[3] = (ix[1] + a1) ^ x1;
-      Cx<P> in[4], out[4];
+    constexpr int iters = (nu + NT - 1) / NT;
+    for_units<iters, ROLLED>([&](int k) {
+      const int u = int(threadIdx.x) + k * NT;
+      if (nu % NT == 0 || u < nu) {
+        const int li = u >> nc_log2;
+        const int c0 = ins0i(ins0i(u & ((1 << nc_log2) - 1), op.cbit[0]), op.cbit[1]);
+        int ix[4];
+        ix[0] = gm.idx(li, c0);
+        ix[1] = (ix[0] + a0) ^ x0;
+        ix[2] = (ix[0] + a1) ^ x1;
+        ix[3] = (ix[1] + a1) ^ x1;
+        Cx<P> in[4], out[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) in[a] = ld<P>(sm, ix[a]);
-      if (op.kind == OP_MONO2) matvec4_mono<P, true>(in, out, cf + 32);
-      else matvec4<P, true>(in, out, cf);
+        for (int a = 0; a < 4; ++a) in[a] = ld<P>(sm, ix[a]);
+        if constexpr (MONO) matvec4_mono<P, true>(in, out, cf + 32);
+        else matvec4<P, true>(in, out, cf);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) st<P>(sm, ix[a], out[a]);
-    }
+        for (int a = 0; a < 4; ++a) st<P>(sm, ix[a], out[a]);
+      }
+    });
   }
   __syncthreads();
   {
@@ -416,37 +448,52 @@ __device__ __forceinline__ void apply_u2_sep(typename P::Elem* sm, const G& gm, 
     gm.row_delta(op.rbit[0], a0, x0);
     gm.row_delta(op.rbit[1], a1, x1);
     constexpr int nu = 1 << (rows_log2g - 2 + cols_log2g);
-#pragma unroll(P::kOpUnroll)
-    for (int u = threadIdx.x; u < nu; u += NT) {
-      const int lj = u & ((1 << cols_log2g) - 1);
-      const int r0 = ins0i(ins0i(u >> cols_log2g, op.rbit[0]), op.rbit[1]);
-      int ix[4];
-      ix[0] = gm.idx(r0, lj);
-      ix[1] = (ix[0] + a0) ^ x0;
-      ix[2] = (ix[0] + a1) ^ x1;
-      ix[3] = (ix[1] + a1) ^ x1;
-      Cx<P> in[4], out[4];
+    constexpr int iters = (nu + NT - 1) / NT;
+    for_units<iters, ROLLED>([&](int k) {
+      const int u = int(threadIdx.x) + k * NT;
+      if (nu % NT == 0 || u < nu) {
+        const int lj = u & ((1 << cols_log2g) - 1);
+        const int r0 = ins0i(ins0i(u >> cols_log2g, op.rbit[0]), op.rbit[1]);
+        int ix[4];
+        ix[0] = gm.idx(r0, lj);
+        ix[1] = (ix[0] + a0) ^ x0;
+        ix[2] = (ix[0] + a1) ^ x1;
+        ix[3] = (ix[1] + a1) ^ x1;
+        Cx<P> in[4], out[4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) in[a] = ld<P>(sm, ix[a]);
-      if (op.kind == OP_MONO2) matvec4_mono<P, false>(in, out, cf + 32);
-      else matvec4<P, false>(in, out, cf);
+        for (int a = 0; a < 4; ++a) in[a] = ld<P>(sm, ix[a]);
+        if constexpr (MONO) matvec4_mono<P, false>(in, out, cf + 32);
+        else matvec4<P, false>(in, out, cf);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) st<P>(sm, ix[a], out[a]);
-    }
+        for (int a = 0; a < 4; ++a) st<P>(sm, ix[a], out[a]);
+      }
+    });
   }
+}
+
+template <class P, class G, int NT, int rows_log2g, int cols_log2g, bool ROLLED = false>
+__device__ __forceinline__ void apply_u2_sep(typename P::Elem* sm, const G& gm, const PassOp& op,
+                                             const double* coef) {
+  const double* cf = coef + op.coef;
+  if (op.kind == OP_MONO2) apply_u2_sep_form<P, G, NT, rows_log2g, cols_log2g, ROLLED, true>(sm, gm, op, cf);
+  else apply_u2_sep_form<P, G, NT, rows_log2g, cols_log2g, ROLLED, false>(sm, gm, op, cf);
 }
 
 template <class P, class G, int NT, int rows_log2g, int cols_log2g>
 __device__ __forceinline__ void apply_ptm2(typename P::Elem* sm, const G& gm, const PassOp& op, const double* coef) {
-  const int ncb_log2 = cols_log2g - 2;
-  const int nb = 1 << (rows_log2g - 2 + ncb_log2);
+  constexpr int ncb_log2 = cols_log2g - 2;
+  constexpr int nb = 1 << (rows_log2g - 2 + ncb_log2);
+  constexpr int iters = (nb + NT - 1) / NT;
   const double* cf = coef + op.coef;
   int ra0, rx0, ra1, rx1, ca0, cx0, ca1, cx1;
   gm.row_delta(op.rbit[0], ra0, rx0);
   gm.row_delta(op.rbit[1], ra1, rx1);
   gm.col_delta(op.cbit[0], ca0, cx0);
   gm.col_delta(op.cbit[1], ca1, cx1);
-  for (int b = threadIdx.x; b < nb; b += NT) {
+#pragma unroll 1
+  for (int k = 0; k < iters; ++k) {
+    const int b = int(threadIdx.x) + k * NT;
+    if (nb % NT != 0 && b >= nb) break;
     const int c0 = ins0i(ins0i(b & ((1 << ncb_log2) - 1), op.cbit[0]), op.cbit[1]);
     const int r0 = ins0i(ins0i(b >> ncb_log2, op.rbit[0]), op.rbit[1]);
     int rowi[4], ix[16];
@@ -647,9 +694,9 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
     }
     for (int o = 0; o < d.nops; ++o) {
       const PassOp& op = d.ops[o];
-      if (op.nq == 1) apply_1q<P, G, kMainThreads, rows_log2g, cols_log2g>(sm, gm, op, d.coef);
+      if (op.nq == 1) apply_1q<P, G, kMainThreads, rows_log2g, cols_log2g, P2>(sm, gm, op, d.coef);
       else if (!P2 || op.kind == OP_U2 || op.kind == OP_MONO2)
-        apply_u2_sep<P, G, kMainThreads, rows_log2g, cols_log2g>(sm, gm, op, d.coef);
+        apply_u2_sep<P, G, kMainThreads, rows_log2g, cols_log2g, P2>(sm, gm, op, d.coef);
       else if constexpr (P2) apply_ptm2<P, G, kMainThreads, rows_log2g, cols_log2g>(sm, gm, op, d.coef);
       __syncthreads();
     }
