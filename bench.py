@@ -98,6 +98,38 @@ def barrier():
         dist.barrier()
 
 
+# ------------------------------------------------------------------ host placement
+def parse_cpulist(spec: str) -> set:
+    """The CPU set of a Linux cpulist string such as "0-3,8,10-11"."""
+    cpus = set()
+    for part in spec.strip().split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
+def bind_near_gpu(torch, dev: int):
+    """Run this process on the CPU cores local to the GPU (its PCI device's
+    local_cpulist), so that pinned host buffers are first touched on the NUMA
+    node the GPU is attached to.  Returns the bound core count, or None when
+    the topology is not exposed."""
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        bdf = f"{int(pr.pci_domain_id):04x}:{int(pr.pci_bus_id):02x}:{int(pr.pci_device_id):02x}.0"
+        with open(f"/sys/bus/pci/devices/{bdf}/local_cpulist") as f:
+            cpus = parse_cpulist(f.read())
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return len(cpus)
+    except (AttributeError, OSError, ValueError):
+        return None
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -712,6 +744,7 @@ def main(argv=None):
         dist.init_process_group("nccl")
     else:
         torch.cuda.set_device(0)
+    bound_cores = bind_near_gpu(torch, torch.cuda.current_device())
     from paper_2604_15765_gb300 import build as _b
     _b.build()
     from paper_2604_15765_gb300 import circuit
@@ -884,7 +917,7 @@ def main(argv=None):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_units / e2e_tot, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h, "host_cores_near_gpu": bound_cores},
             "gpu_launches": launches,
             "clocks": clocks,
             "variants": variants,

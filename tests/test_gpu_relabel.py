@@ -193,3 +193,18 @@ def test_graph_replay_needs_the_captured_labels():
             ok.orkan_graph_free(g)
     finally:
         ok.orkan_free(h)
+
+
+def test_relabel_rejects_bad_maps():
+    n = 5
+    h = ok.orkan_alloc(n, DT["c128"], 3)
+    try:
+        ok.orkan_init_state(h, ok.ORKAN_INIT_MAXMIXED)
+        for bad in ([0, 1, 2, 3, 3], [0, 1, 2, 3, 5], [-1, 0, 1, 2, 3]):
+            with pytest.raises(ok.OrkanError):
+                ok.orkan_relabel(h, bad)
+            assert ok.orkan_get_labels(h, n) == list(range(n))
+        with pytest.raises(ok.OrkanError):
+            ok.orkan_set_relabel(h, 2)
+    finally:
+        ok.orkan_free(h)

@@ -46,3 +46,10 @@ def test_aggregate_sum_over_max_gloo():
         assert units == pytest.approx(300.0)
         assert secs == pytest.approx(2.5)
         assert rc == 0
+
+
+def test_cpulist_parsing():
+    import bench
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("5") == {5}
+    assert bench.parse_cpulist("") == set()
