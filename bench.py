@@ -56,7 +56,7 @@ def parse_args(argv=None):
     p.add_argument("--no-variants", action="store_true", help="skip the c128 / c64 / unfused comparison runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=20.0)
-    p.add_argument("--workload", choices=["sweep", "serving", "brickwork", "precision", "paper", "relabel"],
+    p.add_argument("--workload", choices=["sweep", "serving", "brickwork", "precision", "paper", "relabel", "pipes"],
                    default="sweep")
     p.add_argument("--depth", type=int, default=40)
     p.add_argument("--serve-requests", type=int, default=160,
@@ -131,6 +131,14 @@ def bind_near_gpu(torch, dev: int):
 
 
 # ------------------------------------------------------------------ clocks
+def gpu_uuid(torch, local: int) -> str:
+    """nvidia-smi id of the current device (its UUID, else the local index)."""
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    except Exception:  # noqa: BLE001  (older torch without uuid)
+        return str(local)
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -757,6 +765,18 @@ def main(argv=None):
         tab = per_op_table(ok, wl, n, m, (args.dtype,), stream, torch, reps=args.steps, only=args.op_class)
         print(json.dumps({"op_class": args.op_class, "dtype": args.dtype, "n": n, "pass_GBps": tab[args.dtype]}))
         return 0
+    if args.workload == "pipes":
+        # the measured pipe rates behind the derived ALU peaks (per SM per clock at the sampled SM clock)
+        scratch = torch.empty(4 << 30, dtype=torch.uint8, device="cuda")
+        with ClockSampler(gpu_uuid(torch, local)) as cs:
+            rates = ok.orkan_probe_pipes(scratch.data_ptr(), scratch.numel())
+        clocks = cs.summary()
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        mhz = clocks.get("sm_mhz") or 2070.0
+        per = {k.replace("_per_s", "_per_sm_clk"): round(v / sms / (mhz * 1e6), 2) for k, v in rates.items() if k.endswith("_per_s")}
+        print(json.dumps({"workload": "pipes", "sms": sms, "rates": rates, "per_sm_per_clock": per, "clocks": clocks,
+                          "derived_alu_peaks_T": ALU_PEAK_TOPS}), flush=True)
+        return 0
     if args.workload in ("brickwork", "precision", "paper", "relabel"):
         if args.workload == "relabel":
             rl = relabel_study(ok, circuit, torch, stream, n=16 if args.n == 14 else args.n, depth=args.depth)
@@ -816,10 +836,7 @@ def main(argv=None):
     runner = Runner(ok, circuit, wl, n, m, args.dtype, args.fusion, compose, stream)
 
     # ---- device-resident throughput
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
-    except Exception:
-        gpu_id = str(local)
+    gpu_id = gpu_uuid(torch, local)
     with ClockSampler(gpu_id) as clk:
         ms, pass_ms, pass_cnt, launches = time_steps(runner, args.steps, args.warmup, torch)
     clocks = clk.summary()
@@ -834,14 +851,22 @@ def main(argv=None):
     ok.orkan_store_tiled(runner.O, host_O.numpy())
     e2e_steps = max(2, args.steps // 2)
 
+    phase = {"upload_s": 0.0, "step_s": 0.0}
+
     def e2e_step():
+        ta = time.perf_counter()
         ok.orkan_load_tiled(runner.rho, host_rho.numpy(), ok.ORKAN_STATE)
-        ok.orkan_load_tiled(runner.O, host_O.numpy(), ok.ORKAN_OBSERVABLE)
-        return runner.step()
+        ok.orkan_load_tiled(runner.O, host_O.numpy(), ok.ORKAN_OBSERVABLE)   # both return after their copies
+        tb = time.perf_counter()
+        res = runner.step()                                                  # ends with blocking readouts
+        phase["upload_s"] += tb - ta
+        phase["step_s"] += time.perf_counter() - tb
+        return res
 
     e2e_step()
     torch.cuda.synchronize()
     barrier()
+    phase.update(upload_s=0.0, step_s=0.0)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
@@ -917,7 +942,9 @@ def main(argv=None):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_units / e2e_tot, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "host_cores_near_gpu": bound_cores},
+                    "d2h_bytes_per_step": d2h, "host_cores_near_gpu": bound_cores,
+                    "upload_ms_per_step": round(1e3 * phase["upload_s"] / e2e_steps, 2),
+                    "compute_ms_per_step": round(1e3 * phase["step_s"] / e2e_steps, 2)},
             "gpu_launches": launches,
             "clocks": clocks,
             "variants": variants,

@@ -346,6 +346,16 @@ int orkan_pass_time(orkan_h h, double *ms, int64_t *count);
  * and data movement excluded); bytes = 2 x stored bytes per pass. */
 int orkan_pass_work(orkan_h h, double *alu_ops, double *bytes);
 
+/* Measure the current GPU's arithmetic pipes and copy bandwidth (the
+ * denominators of ALU and HBM rooflines): out[0] FP32 FMA, out[1] FP64 FMA,
+ * out[2] FP32 add, out[3] FP64 add (instructions per second, each from 8
+ * independent dependency chains per thread on 8 CTAs per SM), out[4] the read +
+ * write bandwidth (GB/s) of a grid-stride copy of 16-byte elements.  scratch:
+ * caller-owned device memory, at least 32 MiB (more gives a steadier copy
+ * figure; 4 GiB is far beyond the L2).  Blocks for about a second; runs on the
+ * legacy default stream.  Not part of any operation's path. */
+int orkan_probe_pipes(double *out, void *scratch, size_t scratch_bytes);
+
 /* ------------------------------------------------------------------ allocation-free readout
  * The paper has no counterpart to this entry point; it exists for callers that
  * must not allocate device memory themselves -- e.g. code that runs while a

@@ -94,6 +94,7 @@ _SIGS = {
     "orkan_pass_work": (C.c_int, [_h, _pd, _pd]),
     "orkan_expect_paulis_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_char_p, _pd,
                                               C.c_void_p]),
+    "orkan_probe_pipes": (C.c_int, [_pd, C.c_void_p, C.c_size_t]),
     "orkan_relabel": (C.c_int, [_h, _pi]),
     "orkan_get_labels": (C.c_int, [_h, _pi]),
     "orkan_set_relabel": (C.c_int, [_h, C.c_int]),
@@ -370,6 +371,14 @@ def orkan_expect_paulis_noalloc(dev_state: int, n: int, dtype: int, tile_log2: i
     _check(_lib.orkan_expect_paulis_noalloc(C.c_void_p(dev_state), n, dtype, tile_log2, len(paulis), s, _dptr(out),
                                             C.c_void_p(stream_ptr or 0)), "orkan_expect_paulis_noalloc")
     return out
+
+
+def orkan_probe_pipes(scratch_ptr: int, scratch_bytes: int) -> dict:
+    """Measured pipe rates (instructions/s) and copy bandwidth (GB/s) of the current GPU."""
+    out = (C.c_double * 5)()
+    _check(_lib.orkan_probe_pipes(out, C.c_void_p(scratch_ptr), scratch_bytes), "orkan_probe_pipes")
+    return {"fp32_fma_per_s": out[0], "fp64_fma_per_s": out[1], "fp32_add_per_s": out[2], "fp64_add_per_s": out[3],
+            "copy_GBps": out[4]}
 
 
 # ------------------------------------------------------------------ qubit relabelling
