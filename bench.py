@@ -365,7 +365,8 @@ def per_op_table(ok, wl, n, m, dtypes, stream, torch, reps=4, only=None):
 def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=True):
     """Continuous batching vs one-at-a-time plain FP64 on the same requests.
     Capacity: all requests present at t = 0; latency runs: Poisson arrivals at
-    a fraction of the measured capacity (arrival times rescaled)."""
+    a fraction of the measured capacity (arrival times rescaled), served in
+    arrival order (fifo) and shortest-estimated-work first (sjf)."""
     from paper_2604_15765_gb300 import serving
     served_map = {"c128": "df64"}
     out = {"requests": len(reqs), "slots": slots, "memory_budget_bytes": budget,
@@ -379,6 +380,8 @@ def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=
         scaled = [dict(r, t=r["t"] * (len(reqs) / rate) / span) for r in reqs]
         _, st = serving.serve(scaled, budget, slots=slots, dtype_map=served_map, realtime=True)
         out[f"served_at_{frac:.1f}x_capacity"] = st
+        _, st = serving.serve(scaled, budget, slots=slots, dtype_map=served_map, realtime=True, policy="sjf")
+        out[f"served_at_{frac:.1f}x_capacity_sjf"] = st
     if baseline:
         _, b = serving.serve(reqs, budget, slots=1, dtype_map={"c64": "c128"}, fusion=1, compose=False,
                              realtime=False)

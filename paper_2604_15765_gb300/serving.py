@@ -24,6 +24,7 @@ depend only on the request's own operator, never on what else is running.
 from __future__ import annotations
 
 import collections
+import heapq
 import threading
 import time
 
@@ -115,31 +116,52 @@ def run_request(pool: HandlePool, req, dtype_map=None, fusion=8, compose=True):
     return out
 
 
+def request_cost(req) -> float:
+    """Estimated device work of a request: ops x stored elements (~4^n)."""
+    return float(len(req["ops"])) * 4.0 ** req["n"]
+
+
 def serve(requests, budget_bytes, slots=8, dtype_map=None, fusion=8, compose=True, realtime=True,
-          tile_log2=5):
+          tile_log2=5, policy="fifo"):
     """Continuous batching: requests become eligible at their arrival time
-    (offsets from the start when ``realtime``), are admitted in arrival order
-    when a slot is free and their bytes fit the budget, and run concurrently.
-    Returns (results by request id, stats)."""
+    (offsets from the start when ``realtime``), are admitted when a slot is
+    free and their bytes fit the budget, and run concurrently.  ``policy``
+    orders the eligible requests: "fifo" by arrival, "sjf" shortest estimated
+    work first (``request_cost``; ties by arrival).  Returns (results by
+    request id, stats)."""
+    if policy not in ("fifo", "sjf"):
+        raise ValueError(policy)
     pool = HandlePool(budget_bytes, tile_log2)
     order = sorted(requests, key=lambda r: r["t"])
-    nxt = [0]
+    arrived = [0]          # requests of `order` moved to the eligible heap so far
+    eligible = []          # (key, seq, request)
     qlock = threading.Lock()
     results, lat = {}, {}
     errors = []
     t0 = time.perf_counter()
 
-    def worker():
+    def take():
+        """The next request to run, or None when every request has been taken."""
         while True:
             with qlock:
-                if nxt[0] >= len(order):
-                    return
-                req = order[nxt[0]]
-                nxt[0] += 1
-            if realtime:
-                wait = req["t"] - (time.perf_counter() - t0)
-                if wait > 0:
-                    time.sleep(wait)
+                now = time.perf_counter() - t0
+                while arrived[0] < len(order) and (not realtime or order[arrived[0]]["t"] <= now):
+                    r = order[arrived[0]]
+                    key = request_cost(r) if policy == "sjf" else r["t"]
+                    heapq.heappush(eligible, (key, arrived[0], r))
+                    arrived[0] += 1
+                if eligible:
+                    return heapq.heappop(eligible)[2]
+                if arrived[0] >= len(order):
+                    return None
+                wait = order[arrived[0]]["t"] - now
+            time.sleep(max(wait, 0.0))
+
+    def worker():
+        while True:
+            req = take()
+            if req is None:
+                return
             arrival = t0 + req["t"] if realtime else t0
             try:
                 res = run_request(pool, req, dtype_map, fusion, compose)
@@ -163,5 +185,5 @@ def serve(requests, budget_bytes, slots=8, dtype_map=None, fusion=8, compose=Tru
     ops = sum(len(r["ops"]) for r in requests)
     stats = {"requests": len(results), "elapsed_s": elapsed, "solves_per_s": len(results) / elapsed,
              "ops_per_s": ops / elapsed, "p50_ms": float(np.percentile(lv, 50) * 1e3),
-             "p99_ms": float(np.percentile(lv, 99) * 1e3), "slots": slots}
+             "p99_ms": float(np.percentile(lv, 99) * 1e3), "slots": slots, "policy": policy}
     return results, stats

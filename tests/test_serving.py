@@ -17,10 +17,11 @@ def _requests(count=36):
     return S.serving_stream(count=count, seed=S.BASE_SEED + 40, rate=2000.0, n_range=(3, 9), depth_range=(8, 40))
 
 
-def test_results_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("policy", ["fifo", "sjf"])
+def test_results_same_alone_and_in_the_mix(policy):
     reqs = _requests()
     budget = 2 << 30
-    mixed, stats = serving.serve(reqs, budget, slots=6, dtype_map={"c128": "df64"}, realtime=True)
+    mixed, stats = serving.serve(reqs, budget, slots=6, dtype_map={"c128": "df64"}, realtime=True, policy=policy)
     assert stats["requests"] == len(reqs)
     pool = serving.HandlePool(budget)
     try:
@@ -53,3 +54,23 @@ def test_admission_respects_memory_budget():
     one = max(ok.orkan_bytes(r["n"], 0, 5) for r in reqs) * 2
     res, stats = serving.serve(reqs, one, slots=4, realtime=False)   # only one request fits at a time
     assert stats["requests"] == len(reqs)
+
+
+def test_sjf_orders_by_estimated_work():
+    """Host-only ordering check: with every request present at the start and
+    one slot, sjf runs them in increasing ops x 4^n."""
+    reqs = _requests(10)
+    done = []
+    orig = serving.run_request
+
+    def record(pool, req, *a, **k):
+        done.append(req["id"])
+        return orig(pool, req, *a, **k)
+
+    serving.run_request = record
+    try:
+        serving.serve(reqs, 2 << 30, slots=1, realtime=False, policy="sjf")
+    finally:
+        serving.run_request = orig
+    costs = {r["id"]: serving.request_cost(r) for r in reqs}
+    assert [costs[i] for i in done] == sorted(costs[i] for i in done)
