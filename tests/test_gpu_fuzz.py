@@ -62,7 +62,7 @@ def _random_circuit(rng, n, depth, picture):
     return ops
 
 
-CASES = list(range(48))
+CASES = list(range(160))
 
 
 @pytest.mark.parametrize("case", CASES)
