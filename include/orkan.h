@@ -9,8 +9,11 @@
  *     acting on any hermitian H (a density matrix or an observable).
  *   - Sec. I / Sec. II: the Heisenberg picture applies the trace-dual map
  *       Phi*(O) = sum_alpha K_alpha^dagger O K_alpha.
- *   - Sec. II-A, Eq. (2): a k-local operation K = I (x) L updates every
- *     2^k x 2^k block h_{s,s'} independently: h -> sum L h L^dagger.
+ *   - Sec. II-A, Eq. (2), Algorithm 1: a k-local operation K = I (x) L
+ *     updates every 2^k x 2^k block h_{s,s'} independently:
+ *     h -> sum L h L^dagger (k = 1, 2, 3 here).
+ *   - Sec. III-A: the packed column-major lower triangle, kept as the
+ *     comparison layout (orkan_packed_*).
  *   - Sec. III-B: storage keeps the lower triangle at tile granularity
  *     (tiles of edge M = 2^m, tile (ti, tj) with ti >= tj, tiles row-major,
  *     elements row-major in a tile, diagonal tiles complete, zero padding to
@@ -45,7 +48,7 @@ extern "C" {
 #endif
 
 #define ORKAN_OK 0
-#define ORKAN_EINVAL (-1)    /* bad argument: qubit out of range or repeated, k > 2, r > 4^k, ... */
+#define ORKAN_EINVAL (-1)    /* bad argument: qubit out of range or repeated, k > 3, r > 4^k, ... */
 #define ORKAN_ENOMEM (-2)    /* device or host allocation failed */
 #define ORKAN_ECUDA (-3)     /* a CUDA call failed (message in orkan_last_error) */
 #define ORKAN_EZEROPROB (-4) /* measurement: the selected outcome has probability < 1e-300 */
@@ -148,7 +151,9 @@ int orkan_get_info(orkan_h h, int *n, int *dtype, int *tile_log2, int *picture);
  * Errors: EINVAL, ENODEV, ENOMEM, ECUDA.  (Not in the paper, which fixes m = 5.) */
 int orkan_autotune(int n, int dtype, int *tile_log2, int *max_ops);
 
-/* Device address of the tiled array (layout of Sec. III-B, element type of the dtype). */
+/* Device address of the tiled array (layout of Sec. III-B, element type of the
+ * dtype), indexed by physical qubit labels (the identity unless orkan_relabel
+ * or the automatic planner moved qubits; see orkan_get_labels). */
 void *orkan_device_ptr(orkan_h h);
 
 /* ------------------------------------------------------------------ initialisation */
