@@ -5,9 +5,11 @@
 // (i, j) with i < j of the operator is the conjugate of (j, i); inside a
 // diagonal tile both are stored and the lower one is authoritative.
 //
-// Reductions accumulate in FP64 for every storage policy and are
-// deterministic: a fixed grid of kRedBlocks CTAs, a fixed per-thread order,
-// a fixed shuffle tree, and a single-CTA final pass in index order.
+// Reductions accumulate in FP64 for every storage policy (the tiled mean value
+// forms its per-tile partial sums of DF64 / C64 products in double-float, see
+// TileDot) and are deterministic: a fixed grid of kRedBlocks CTAs, a fixed
+// per-thread order, a fixed shuffle tree, and a single-CTA final pass in index
+// order.
 #include "orkan_internal.h"
 #include "numeric.cuh"
 #include "device_util.cuh"
@@ -206,6 +208,35 @@ __global__ void k_reduce_pauli(const typename P::Elem* st, int m, int64_t N, uin
   block_reduce_store<2>(v, partials + 2 * blockIdx.x);
 }
 
+// a.re b.re + a.im b.im summed over one thread's
+// elements of one tile.  C128 accumulates in FP64.  DF64 and C64 form the
+// products on the FP32 pipe (TwoProduct of the leading parts plus the cross
+// terms) and accumulate them in double-float (TwoSum), converting to FP64 once
+// per tile: GB300's FP64 pipe would otherwise bind this HBM-streaming reduction
+// (converting every double-float element costs ~14 FP64 operations).
+template <class P> struct TileDot;
+template <> struct TileDot<PolF64> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(const double2& a, const double2& b) { s = fma(a.x, b.x, fma(a.y, b.y, s)); }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct TileDot<PolDF64> {
+  DF acc{0.0f, 0.0f};
+  __device__ __forceinline__ void add(const float4& a, const float4& b) {
+    acc = PolDF64::mac(acc, DF{a.x, a.y}, make_float2(b.x, b.y));
+    acc = PolDF64::mac(acc, DF{a.z, a.w}, make_float2(b.z, b.w));
+  }
+  __device__ __forceinline__ double get() const { return double(acc.hi) + double(acc.lo); }
+};
+template <> struct TileDot<PolF32> {
+  DF acc{0.0f, 0.0f};
+  __device__ __forceinline__ void add(const float2& a, const float2& b) {
+    acc = PolDF64::mac(acc, DF{a.x, 0.0f}, make_float2(b.x, 0.0f));
+    acc = PolDF64::mac(acc, DF{a.y, 0.0f}, make_float2(b.y, 0.0f));
+  }
+  __device__ __forceinline__ double get() const { return double(acc.hi) + double(acc.lo); }
+};
+
 template <class P>
 __global__ void k_reduce_expect(const typename P::Elem* rho, const typename P::Elem* O, int m, int64_t ntiles,
                                 double* partials) {
@@ -214,12 +245,9 @@ __global__ void k_reduce_expect(const typename P::Elem* rho, const typename P::E
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t ti = tri_row(t), tj = t - ti * (ti + 1) / 2;
     const int64_t base = t << (2 * m);
-    double s = 0.0;
-    for (int w = threadIdx.x; w < MM; w += blockDim.x) {
-      const double2 a = Conv<P>::to(rho[base + w]);
-      const double2 b = Conv<P>::to(O[base + w]);
-      s = fma(a.x, b.x, fma(a.y, b.y, s));
-    }
+    TileDot<P> dot;
+    for (int w = threadIdx.x; w < MM; w += blockDim.x) dot.add(rho[base + w], O[base + w]);
+    const double s = dot.get();
     v[0] += (ti == tj) ? s : 2.0 * s;
   }
   block_reduce_store<1>(v, partials + blockIdx.x);
