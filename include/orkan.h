@@ -59,9 +59,10 @@ extern "C" {
  *   ORKAN_C128: complex128 elements, native FP64 arithmetic (16 B/element).
  *   ORKAN_C64 : complex64 elements, FP32 arithmetic (8 B/element).
  *   ORKAN_DF64: "double-float" elements -- real and imaginary part each kept
- *               as an unevaluated sum hi + lo of two floats (16 B/element) --
- *               with FP32-pipe error-free arithmetic, about 48 significand
- *               bits.  Values must stay within the float exponent range
+ *               as an unevaluated sum hi + lo of two floats (16 B/element,
+ *               stored as the floats re.hi, im.hi, re.lo, im.lo) -- with
+ *               FP32-pipe error-free arithmetic, about 48 significand bits.
+ *               Values must stay within the float exponent range
  *               (|x| < 3e38; parts below 1e-38 flush to zero).
  * Readouts (trace, probabilities, expectations) accumulate in FP64 for all. */
 #define ORKAN_C128 0

@@ -220,13 +220,17 @@ template <> struct TileDot<PolF64> {
   __device__ __forceinline__ void add(const double2& a, const double2& b) { s = fma(a.x, b.x, fma(a.y, b.y, s)); }
   __device__ __forceinline__ double get() const { return s; }
 };
+// Elements (re.hi, im.hi, re.lo, im.lo): the real-part products accumulate in
+// lane 0 and the imaginary-part products in lane 1 of one paired sum.
 template <> struct TileDot<PolDF64> {
-  DF acc{0.0f, 0.0f};
+  DF2 acc{make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
   __device__ __forceinline__ void add(const float4& a, const float4& b) {
-    acc = PolDF64::mac(acc, DF{a.x, a.y}, make_float2(b.x, b.y));
-    acc = PolDF64::mac(acc, DF{a.z, a.w}, make_float2(b.z, b.w));
+    acc = df2_mac(acc, DF2{make_float2(a.x, a.y), make_float2(a.z, a.w)},
+                  DF2{make_float2(b.x, b.y), make_float2(b.z, b.w)});
   }
-  __device__ __forceinline__ double get() const { return double(acc.hi) + double(acc.lo); }
+  __device__ __forceinline__ double get() const {
+    return (double(acc.hi.x) + double(acc.lo.x)) + (double(acc.hi.y) + double(acc.lo.y));
+  }
 };
 template <> struct TileDot<PolF32> {
   DF acc{0.0f, 0.0f};

@@ -29,13 +29,14 @@ template <> struct Conv<PolF32> {
   static __device__ __forceinline__ float2 from(double re, double im) { return make_float2((float)re, (float)im); }
 };
 template <> struct Conv<PolDF64> {
+  // element order (re.hi, im.hi, re.lo, im.lo)
   static __device__ __forceinline__ double2 to(float4 e) {
-    return make_double2((double)e.x + (double)e.y, (double)e.z + (double)e.w);
+    return make_double2((double)e.x + (double)e.z, (double)e.y + (double)e.w);
   }
   static __device__ __forceinline__ float4 from(double re, double im) {
     const float rh = __double2float_rn(re), ih = __double2float_rn(im);
     const float rl = __double2float_rn(re - (double)rh), il = __double2float_rn(im - (double)ih);
-    return make_float4(rh, rl, ih, il);
+    return make_float4(rh, ih, rl, il);
   }
 };
 

@@ -11,6 +11,12 @@
 //
 // GB300 runs FP64 at ~1/64 of the FP32 rate, so only the FP32 pipe can keep a
 // conjugation pass at HBM speed; PolDF64 trades 5 bits of precision for that.
+//
+// A PolDF64 element is stored as (re.hi, im.hi, re.lo, im.lo): one 16-byte
+// load yields the pairs (re.hi, im.hi) and (re.lo, im.lo), which the hot op
+// bodies feed to Blackwell's paired FP32 instructions (f32x2: one instruction
+// per two lanes), so that the real and imaginary parts of a complex value
+// share every double-float step.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -98,7 +104,7 @@ __device__ __forceinline__ DF df_fast_two_sum(float a, float b) {
 }
 
 struct PolDF64 {
-  using Elem = float4;   // (re.hi, re.lo, im.hi, im.lo)
+  using Elem = float4;   // (re.hi, im.hi, re.lo, im.lo)
   using Real = DF;
   using Coef = float2;   // (hi, lo) split of an FP64 coefficient, made on the host
   static constexpr int kSwizzle = 7;
@@ -107,14 +113,14 @@ struct PolDF64 {
     return reinterpret_cast<const float2*>(c)[i];
   }
   static __device__ __forceinline__ Elem conj_if(Elem e, unsigned t) {
-    e.z = __int_as_float(__float_as_int(e.z) ^ int(t << 31));
+    e.y = __int_as_float(__float_as_int(e.y) ^ int(t << 31));
     e.w = __int_as_float(__float_as_int(e.w) ^ int(t << 31));
     return e;
   }
-  static __device__ __forceinline__ Real re(const Elem& e) { return {e.x, e.y}; }
-  static __device__ __forceinline__ Real im(const Elem& e) { return {e.z, e.w}; }
-  static __device__ __forceinline__ Elem make(Real r, Real i) { return make_float4(r.hi, r.lo, i.hi, i.lo); }
-  static __device__ __forceinline__ Elem conj(Elem e) { e.z = -e.z; e.w = -e.w; return e; }
+  static __device__ __forceinline__ Real re(const Elem& e) { return {e.x, e.z}; }
+  static __device__ __forceinline__ Real im(const Elem& e) { return {e.y, e.w}; }
+  static __device__ __forceinline__ Elem make(Real r, Real i) { return make_float4(r.hi, i.hi, r.lo, i.lo); }
+  static __device__ __forceinline__ Elem conj(Elem e) { e.y = -e.y; e.w = -e.w; return e; }
   static __device__ __forceinline__ Real add(Real a, Real b) {
     DF s = df_two_sum(a.hi, b.hi);
     return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
@@ -153,5 +159,96 @@ template <class P>
 struct Cx {
   typename P::Real re, im;
 };
+
+// ------------------------------------------------------------------ paired double-float
+// A complex double-float value with its real and imaginary parts in the two
+// lanes of f32x2 operands: hi = (re.hi, im.hi), lo = (re.lo, im.lo).  Every
+// operation is the PolDF64 operation above applied to both lanes at once
+// (same rounding, same results), with half the instructions.
+struct DF2 {
+  float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, f2neg(b)); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2swap(float2 a) { return make_float2(a.y, a.x); }
+
+// Fast2Sum on both lanes (exact when |a| >= |b| lane-wise or a == 0).
+__device__ __forceinline__ DF2 df2_fast(float2 a, float2 b) {
+  const float2 s = f2add(a, b);
+  return {s, f2sub(b, f2sub(s, a))};
+}
+// a + b.  The leading parts are summed by TwoSum, the trailing parts with
+// the error, then renormalised (11 paired instructions).
+__device__ __forceinline__ DF2 df2_add(const DF2& a, const DF2& b) {
+  const float2 s = f2add(a.hi, b.hi);
+  const float2 bb = f2sub(s, a.hi);
+  const float2 e = f2add(f2sub(a.hi, f2sub(s, bb)), f2sub(b.hi, bb));
+  return df2_fast(s, f2add(e, f2add(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF2 df2_neg(const DF2& a) { return {f2neg(a.hi), f2neg(a.lo)}; }
+__device__ __forceinline__ DF2 df2_sub(const DF2& a, const DF2& b) { return df2_add(a, df2_neg(b)); }
+// a + s * b with a lane-wise sign pair s = (+-1, +-1): the product by +-1 is
+// exact, so each FMA below rounds like the add it replaces (same cost as df2_add).
+__device__ __forceinline__ DF2 df2_add_signed(const DF2& a, const DF2& b, float2 sg) {
+  const float2 s = f2fma(b.hi, sg, a.hi);
+  const float2 bb = f2sub(s, a.hi);
+  const float2 e = f2add(f2sub(a.hi, f2sub(s, bb)), f2fma(b.hi, sg, f2neg(bb)));
+  return df2_fast(s, f2add(e, f2fma(b.lo, sg, a.lo)));
+}
+// a + i b and a - i b: i b = (-b.im, b.re), the lane swap of b with sign (-1, +1).
+__device__ __forceinline__ DF2 df2_add_i(const DF2& a, const DF2& b) {
+  return df2_add_signed(a, DF2{f2swap(b.hi), f2swap(b.lo)}, make_float2(-1.0f, 1.0f));
+}
+__device__ __forceinline__ DF2 df2_sub_i(const DF2& a, const DF2& b) {
+  return df2_add_signed(a, DF2{f2swap(b.hi), f2swap(b.lo)}, make_float2(1.0f, -1.0f));
+}
+// x * c with TwoProduct on the leading parts and the two cross terms, left
+// unnormalised; c is a coefficient pair (one factor per lane).
+__device__ __forceinline__ DF2 df2_mul(const DF2& x, const DF2& c) {
+  const float2 p = f2mul(x.hi, c.hi);
+  float2 e = f2fma(x.hi, c.hi, f2neg(p));
+  e = f2fma(x.hi, c.lo, e);
+  e = f2fma(x.lo, c.hi, e);
+  return {p, e};
+}
+// acc + x * c, unnormalised like PolDF64::mac (12 paired instructions).
+__device__ __forceinline__ DF2 df2_mac(const DF2& acc, const DF2& x, const DF2& c) {
+  const float2 p = f2mul(x.hi, c.hi);
+  float2 e = f2fma(x.hi, c.hi, f2neg(p));
+  e = f2fma(x.hi, c.lo, e);
+  e = f2fma(x.lo, c.hi, e);
+  const float2 s = f2add(acc.hi, p);
+  const float2 bb = f2sub(s, acc.hi);
+  const float2 ee = f2add(f2sub(acc.hi, f2sub(s, bb)), f2sub(p, bb));
+  return {s, f2add(ee, f2add(e, acc.lo))};
+}
+// acc + (lane swap of x) * c: with c = (-v, v) this adds v * (i x), with
+// c = (v, -v) it adds -v * (i x).
+__device__ __forceinline__ DF2 df2_mac_swap(const DF2& acc, const DF2& x, const DF2& c) {
+  return df2_mac(acc, DF2{f2swap(x.hi), f2swap(x.lo)}, c);
+}
+__device__ __forceinline__ DF2 df2_norm(const DF2& a) { return df2_fast(a.hi, a.lo); }
+__device__ __forceinline__ DF2 df2_half(const DF2& a) {
+  const float2 h = make_float2(0.5f, 0.5f);
+  return {f2mul(a.hi, h), f2mul(a.lo, h)};
+}
+
+// Conversions between the per-part form Cx<PolDF64> and the paired form.
+__device__ __forceinline__ DF2 to_df2(const Cx<PolDF64>& z) {
+  return {make_float2(z.re.hi, z.im.hi), make_float2(z.re.lo, z.im.lo)};
+}
+__device__ __forceinline__ Cx<PolDF64> from_df2(const DF2& z) {
+  return Cx<PolDF64>{DF{z.hi.x, z.lo.x}, DF{z.hi.y, z.lo.y}};
+}
+// Coefficient pair k of a paired coefficient list: two 8-byte slots,
+// (c0.hi, c1.hi) then (c0.lo, c1.lo), written by the host.
+__device__ __forceinline__ DF2 pcoef(const double* cf, int k) {
+  const float2* p = reinterpret_cast<const float2*>(cf);
+  return {p[2 * k], p[2 * k + 1]};
+}
 
 }  // namespace orkan

@@ -294,7 +294,10 @@ PassShape shape_of(const orkan_ctx* h, const std::vector<HostOp>& ops, const Hos
   return s;
 }
 
-int slots_upper_bound(const HostOp& op) { return op.nq == 1 ? 16 : coef_slots(op.kind); }
+int slots_upper_bound(const orkan_ctx* h, const HostOp& op) {
+  const bool paired = h->dtype == DT_DF64;
+  return op.nq == 1 ? coef_slots(OP_PTM1, paired) : coef_slots(op.kind, paired);
+}
 
 bool fits(const orkan_ctx* h, const HostOp& op) {
   if (h->pending.empty()) return true;
@@ -302,8 +305,8 @@ bool fits(const orkan_ctx* h, const HostOp& op) {
   const PassShape s = shape_of(h, h->pending, &op);
   if (s.nh > 2) return false;
   if (s.max_low >= rows_log2_for(h, s.nh)) return false;
-  int slots = slots_upper_bound(op);
-  for (const auto& p : h->pending) slots += slots_upper_bound(p);
+  int slots = slots_upper_bound(h, op);
+  for (const auto& p : h->pending) slots += slots_upper_bound(h, p);
   return slots <= kMaxCoef;
 }
 
@@ -322,7 +325,43 @@ void pack_slot(int dtype, double* slot, double v) {
   }
 }
 
-void pack_coef(const orkan_ctx* h, PassDesc& d, int slot, double v) { pack_slot(h->dtype, &d.coef[slot], v); }
+// The coefficients c of one op (kind-specific FP64 list) into slots, in the
+// layout its kernel body reads; returns the slots written.  DF64 forms with a
+// paired body (PTM1, PTM1_U, PTM1_AD) take each coefficient use as a lane
+// pair of double-float values, the hi pair then the lo pair: (v, v) for a real
+// factor, (-v, v) where the body multiplies the lane swap (x.im, x.re), i.e.
+// i x, and (v, -v) for -i x.  The other forms and dtypes: one slot each.
+int pack_op_coefs(int dtype, int kind, const std::vector<double>& c, double* slots) {
+  const bool paired = dtype == DT_DF64 && (kind == OP_PTM1 || kind == OP_PTM1_U || kind == OP_PTM1_AD);
+  if (!paired) {
+    for (size_t i = 0; i < c.size(); ++i) pack_slot(dtype, &slots[i], c[i]);
+    return int(c.size());
+  }
+  int k = 0;
+  auto pair = [&](double v0, double v1) {
+    const float h0 = (float)v0, h1 = (float)v1;
+    const float hi[2] = {h0, h1}, lo[2] = {(float)(v0 - (double)h0), (float)(v1 - (double)h1)};
+    std::memcpy(&slots[2 * k], hi, 8);
+    std::memcpy(&slots[2 * k + 1], lo, 8);
+    ++k;
+  };
+  if (kind == OP_PTM1) {            // 4 x 4, column 2 multiplies i (b - c)
+    for (int i = 0; i < 16; ++i) {
+      if (i % 4 == 2) pair(-c[i], c[i]);
+      else pair(c[i], c[i]);
+    }
+  } else if (kind == OP_PTM1_U) {   // 3 x 3, column 1 multiplies i (b - c)
+    for (int i = 0; i < 9; ++i) {
+      if (i % 3 == 1) pair(-c[i], c[i]);
+      else pair(c[i], c[i]);
+    }
+  } else {                          // PTM1_AD: al, be, ga, de, rho; sig for h10 (+i), for h01 (-i)
+    for (int i = 0; i < 5; ++i) pair(c[i], c[i]);
+    pair(-c[5], c[5]);
+    pair(c[5], -c[5]);
+  }
+  return 2 * k;
+}
 
 // Event pair bracketing one timed pass (pooled events); none while capturing.
 int timing_begin(orkan_ctx* h, std::pair<cudaEvent_t, cudaEvent_t>* ev) {
@@ -423,7 +462,7 @@ int flush_pending(orkan_ctx* h) {
       continue;
     }
     const std::vector<double> c = op.nq == 1 ? coef_1q(op.kind, op.R) : op.coef;
-    for (double v : c) pack_coef(h, d, slot++, v);
+    slot += pack_op_coefs(h->dtype, op.kind, c, &d.coef[slot]);
     for (long long v : op.codes) std::memcpy(&d.coef[slot++], &v, 8);
   }
   const int64_t nops = int64_t(h->pending.size());
@@ -1168,14 +1207,13 @@ int packed_run(void* dev, int n, int dtype, const HostOp& op, void* stream) {
       for (int i = 0; i < 4; ++i) std::memcpy(&d.coef[i], &op.codes[i], 8);
     } else {
       d.kind = op.kind;
-      const std::vector<double> c = coef_1q(op.kind, op.R);
-      for (size_t i = 0; i < c.size(); ++i) pack_slot(dtype, &d.coef[i], c[i]);
+      pack_op_coefs(dtype, op.kind, coef_1q(op.kind, op.R), d.coef);
     }
   } else {
     if (op.kind != OP_U2 && op.kind != OP_MONO2)
       return fail(ORKAN_EINVAL, "packed layout: two-qubit maps must be unitary (one Kraus operator)");
     d.kind = op.kind;
-    for (int i = 0; i < 32; ++i) pack_slot(dtype, &d.coef[i], op.coef[i]);
+    pack_op_coefs(dtype, op.kind, std::vector<double>(op.coef.begin(), op.coef.begin() + 32), d.coef);
     for (size_t i = 0; i < op.codes.size(); ++i) std::memcpy(&d.coef[32 + i], &op.codes[i], 8);
   }
   const int64_t S = d.N >> d.k;

@@ -38,11 +38,15 @@ constexpr int kMaxOps = 16;     // ops fused into one pass
 constexpr int kMaxCoef = 640;   // 8-byte coefficient slots per pass
 constexpr int kThreads = 256;   // threads per CTA of the pass kernel
 
-inline int coef_slots(int kind) {
+// Slots of an op's coefficients.  Per-part layout (C128, C64, and the
+// DF64 forms not listed below): one slot per FP64 coefficient.  DF64 paired
+// layout (PTM1, PTM1_U, PTM1_AD): each coefficient use is a lane pair, two
+// slots (hi pair, lo pair) -- see pack_op_coefs.
+inline int coef_slots(int kind, bool paired = false) {
   switch (kind) {
-    case OP_PTM1: return 16;
-    case OP_PTM1_U: return 9;
-    case OP_PTM1_AD: return 6;
+    case OP_PTM1: return paired ? 32 : 16;
+    case OP_PTM1_U: return paired ? 18 : 9;
+    case OP_PTM1_AD: return paired ? 14 : 6;
     case OP_U2: return 32;      // 16 complex entries, re/im interleaved
     case OP_PTM2: return 256;
     case OP_MONO1: return 4;
@@ -78,7 +82,7 @@ struct PassDesc {
   int32_t nops;
   int32_t skip_diag;   // 1: chunked pass; diagonal groups run in pass_kernel_diag
   PassOp ops[kMaxOps];
-  double coef[kMaxCoef];   // F64: double; DF64: float2 (hi, lo); C64: float in the low half
+  double coef[kMaxCoef];   // F64: double; DF64: float2 (hi, lo) or lane pairs; C64: float in the low half
 };
 
 // Three-qubit operations (k = 3): Algorithm 1 on the tiled layout.  One
@@ -113,7 +117,7 @@ struct PackedDesc {
   int32_t k;
   int32_t kind;
   int32_t q[2];       // ascending
-  double coef[40];
+  double coef[40];   // the pass kernels' slots (coef_slots)
 };
 cudaError_t launch_packed(int dtype, void* state, const PackedDesc& d, cudaStream_t stream);
 

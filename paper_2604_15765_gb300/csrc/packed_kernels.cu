@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kPkThreads) k_packed_op(typename P::Elem* __re
       if constexpr (FORM == OP_PTM1_U) body_ptm1_u<P>(h[0], h[1], h[2], h[3], cf);
       else if constexpr (FORM == OP_PTM1_AD) body_ptm1_ad<P>(h[0], h[1], h[2], h[3], cf);
       else if constexpr (FORM == OP_PTM1) body_ptm1<P>(h[0], h[1], h[2], h[3], cf);
-      else body_u2<P>(h, cf);
+      else body_u2<P, false>(h, cf);
     }
     const bool dblk = s == sp;
 #pragma unroll

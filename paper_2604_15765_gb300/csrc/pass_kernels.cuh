@@ -189,62 +189,6 @@ __device__ __forceinline__ void body_mono1(Cx<P>& a, Cx<P>& b, Cx<P>& c, Cx<P>& 
   d = rot_i<P>(pick(p1, p1), q1 - q1);
 }
 
-// Two-qubit unitary, h <- V h V^dagger, in registers: first every row of h is
-// replaced by h[k,:] V^dagger, then every column by V (.)[:, j].
-template <class P>
-__device__ __forceinline__ void body_u2(Cx<P> (&h)[16], const double* cf) {
-  using R = typename P::Real;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    R tr[4], ti[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      // sum_l h[k][l] conj(V[j][l])
-      R accr = P::mul(h[4 * k].re, P::coef(cf, 2 * (4 * j)));
-      accr = P::mac(accr, h[4 * k].im, P::coef(cf, 2 * (4 * j) + 1));
-      R acci = P::mul(h[4 * k].im, P::coef(cf, 2 * (4 * j)));
-      acci = P::mac(acci, P::neg(h[4 * k].re), P::coef(cf, 2 * (4 * j) + 1));
-#pragma unroll
-      for (int l = 1; l < 4; ++l) {
-        const auto vr = P::coef(cf, 2 * (4 * j + l)), vi = P::coef(cf, 2 * (4 * j + l) + 1);
-        accr = P::mac(accr, h[4 * k + l].re, vr);
-        accr = P::mac(accr, h[4 * k + l].im, vi);
-        acci = P::mac(acci, h[4 * k + l].im, vr);
-        acci = P::mac(acci, P::neg(h[4 * k + l].re), vi);
-      }
-      tr[j] = P::norm(accr);
-      ti[j] = P::norm(acci);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) { h[4 * k + j].re = tr[j]; h[4 * k + j].im = ti[j]; }
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    R tr[4], ti[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      // sum_k V[i][k] Y[k][j]
-      const auto v0r = P::coef(cf, 2 * (4 * i)), v0i = P::coef(cf, 2 * (4 * i) + 1);
-      R accr = P::mul(h[j].re, v0r);
-      accr = P::mac(accr, P::neg(h[j].im), v0i);
-      R acci = P::mul(h[j].im, v0r);
-      acci = P::mac(acci, h[j].re, v0i);
-#pragma unroll
-      for (int k = 1; k < 4; ++k) {
-        const auto vr = P::coef(cf, 2 * (4 * i + k)), vi = P::coef(cf, 2 * (4 * i + k) + 1);
-        accr = P::mac(accr, h[4 * k + j].re, vr);
-        accr = P::mac(accr, P::neg(h[4 * k + j].im), vi);
-        acci = P::mac(acci, h[4 * k + j].im, vr);
-        acci = P::mac(acci, h[4 * k + j].re, vi);
-      }
-      tr[i] = P::norm(accr);
-      ti[i] = P::norm(acci);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) { h[4 * i + j].re = tr[i]; h[4 * i + j].im = ti[i]; }
-  }
-}
-
 // Forward / inverse single-qubit Pauli transform on four complex values.
 template <class P>
 __device__ __forceinline__ void pauli_fwd(Cx<P>& a, Cx<P>& b, Cx<P>& c, Cx<P>& d) {
@@ -348,6 +292,103 @@ __device__ __forceinline__ void matvec4_mono(const Cx<P> (&in)[4], Cx<P> (&out)[
     const Cx<P> x = p == 0 ? in[0] : (p == 1 ? in[1] : (p == 2 ? in[2] : in[3]));
     out[i] = rot_i<P>(x, CONJ ? -q : q);
   }
+}
+
+// Two-qubit unitary, h <- V h V^dagger, on a 4x4 block in registers: every
+// row becomes h[k, :] V^dagger, then every column V (.)[:, j] (Eq. 2 with
+// one Kraus operator).  MONO: the monomial form (codes after the dense V).
+template <class P, bool MONO>
+__device__ __forceinline__ void body_u2(Cx<P> (&h)[16], const double* cf) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    Cx<P> in[4], out[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) in[l] = h[4 * k + l];
+    if constexpr (MONO) matvec4_mono<P, true>(in, out, cf + 32);
+    else matvec4<P, true>(in, out, cf);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) h[4 * k + l] = out[l];
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    Cx<P> in[4], out[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) in[l] = h[4 * l + j];
+    if constexpr (MONO) matvec4_mono<P, false>(in, out, cf + 32);
+    else matvec4<P, false>(in, out, cf);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) h[4 * l + j] = out[l];
+  }
+}
+
+// ------------------------------------------------------------------ paired double-float bodies
+// The PolDF64 forms of the single-qubit bodies above: the same operations in
+// the same order on both parts of each complex value at once (f32x2), so the
+// results equal the per-part forms bit for bit.  Their coefficient lists are
+// paired (pcoef, written by the host): a real coefficient c as the pair
+// (c, c); where the per-part form multiplies i t (t a complex value), the
+// pair (-c, c) multiplies the lane swap (t.im, t.re) instead, which gives
+// c (i t) without forming i t.
+//
+// The two-qubit sweeps (matvec4) stay per-part.  Paired, they issued 29 %
+// fewer instructions but ran no faster: merging the real and imaginary
+// chains halves the independent work per thread, the unit loop then has to
+// stay rolled to avoid spills, and with four warps per scheduler the pass
+// becomes latency-bound (measured on a two-high-qubit unitary pass, n = 13).
+
+template <>
+__device__ __forceinline__ void body_ptm1<PolDF64>(Cx<PolDF64>& a, Cx<PolDF64>& b, Cx<PolDF64>& c,
+                                                   Cx<PolDF64>& d, const double* cf) {
+  // coefficient pairs 4 i + j: R_ij / 2, the j = 2 column as (-R, R)
+  const DF2 A = to_df2(a), B = to_df2(b), C = to_df2(c), D = to_df2(d);
+  const DF2 s0 = df2_add(A, D), s1 = df2_add(B, C), t = df2_sub(B, C), s3 = df2_sub(A, D);
+  DF2 z[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    DF2 acc = df2_mul(s0, pcoef(cf, 4 * i));
+    acc = df2_mac(acc, s1, pcoef(cf, 4 * i + 1));
+    acc = df2_mac_swap(acc, t, pcoef(cf, 4 * i + 2));
+    acc = df2_mac(acc, s3, pcoef(cf, 4 * i + 3));
+    z[i] = df2_norm(acc);
+  }
+  a = from_df2(df2_add(z[0], z[3]));
+  d = from_df2(df2_sub(z[0], z[3]));
+  b = from_df2(df2_sub_i(z[1], z[2]));
+  c = from_df2(df2_add_i(z[1], z[2]));
+}
+
+template <>
+__device__ __forceinline__ void body_ptm1_u<PolDF64>(Cx<PolDF64>& a, Cx<PolDF64>& b, Cx<PolDF64>& c,
+                                                     Cx<PolDF64>& d, const double* cf) {
+  // coefficient pairs 3 i + j: R3_ij / 2, the j = 1 column as (-R, R)
+  const DF2 A = to_df2(a), B = to_df2(b), C = to_df2(c), D = to_df2(d);
+  const DF2 s0 = df2_add(B, C), t = df2_sub(B, C), s2 = df2_sub(A, D);
+  const DF2 z0 = df2_half(df2_add(A, D));
+  DF2 z[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    DF2 acc = df2_mul(s0, pcoef(cf, 3 * i));
+    acc = df2_mac_swap(acc, t, pcoef(cf, 3 * i + 1));
+    acc = df2_mac(acc, s2, pcoef(cf, 3 * i + 2));
+    z[i] = df2_norm(acc);
+  }
+  a = from_df2(df2_add(z0, z[2]));
+  d = from_df2(df2_sub(z0, z[2]));
+  b = from_df2(df2_sub_i(z[0], z[1]));
+  c = from_df2(df2_add_i(z[0], z[1]));
+}
+
+template <>
+__device__ __forceinline__ void body_ptm1_ad<PolDF64>(Cx<PolDF64>& a, Cx<PolDF64>& b, Cx<PolDF64>& c,
+                                                      Cx<PolDF64>& d, const double* cf) {
+  // pairs: al, be, ga, de, rho as (c, c); then (-sig, sig) and (sig, -sig)
+  const DF2 A = to_df2(a), B = to_df2(b), C = to_df2(c), D = to_df2(d);
+  const DF2 rh = pcoef(cf, 4);
+  a = from_df2(df2_norm(df2_mac(df2_mul(A, pcoef(cf, 0)), D, pcoef(cf, 1))));
+  d = from_df2(df2_norm(df2_mac(df2_mul(A, pcoef(cf, 2)), D, pcoef(cf, 3))));
+  // h01' = (rho - i sig) h01, h10' = (rho + i sig) h10
+  b = from_df2(df2_norm(df2_mac_swap(df2_mul(B, rh), B, pcoef(cf, 6))));
+  c = from_df2(df2_norm(df2_mac_swap(df2_mul(C, rh), C, pcoef(cf, 5))));
 }
 
 // ------------------------------------------------------------------ op drivers
@@ -816,7 +857,8 @@ __device__ __forceinline__ void diag_apply(typename P::Elem* sm, const DMap& mp,
       for (int ra = 0; ra < 4; ++ra)
 #pragma unroll
         for (int ca = 0; ca < 4; ++ca) h[4 * ra + ca] = dread<P>(sm, mp, rows[ra], cols[ca]);
-      if (op.kind == OP_U2 || op.kind == OP_MONO2) body_u2<P>(h, cf);
+      if (op.kind == OP_U2) body_u2<P, false>(h, cf);
+      else if (op.kind == OP_MONO2) body_u2<P, true>(h, cf);
       else body_ptm2<P>(h, cf);
 #pragma unroll
       for (int ra = 0; ra < 4; ++ra)
