@@ -44,7 +44,14 @@ __device__ __forceinline__ int ins0i(int x, int p) {
 // at row r; the element (16-byte granule) index inside a row is
 // XOR-swizzled with the row so that row-wise and column-wise walks hit
 // distinct banks:
-//   idx = ((x 2^H + y) R + r) M + (c ^ ((r & sw) << SH)).
+//   idx = ((x 2^H + y) R + r) M + (c ^ swz(r)),
+//   swz(r) = ((r & sw) ^ (bit 3 of r ? b3 : 0)) << SH.
+// With 16-byte elements in slots of at least 16 rows, b3 = 7: rows with bit 3
+// set flip all three low granule bits.  Then any eight rows with one of the
+// bits 0..2 clear (the first rows of the 2x2 blocks of a single-qubit op on
+// that bit, walked rows-first) still cover all eight 16-byte bank groups,
+// which the plain row XOR cannot: it keeps that bit clear.  swz is linear
+// over GF(2), so a row partner's swizzle is swz(r) ^ swz(2^pos).
 // Slots whose tile lies in the upper triangle are loaded already transposed
 // and conjugated, so every op sees plain logical elements.
 template <class P, int H, int MLOG, int RL>
@@ -53,15 +60,19 @@ struct GMap {
   static constexpr int R = 1 << RL;
   static constexpr int SH = P::kSwShift;
   static constexpr int SW = ((M >> SH) - 1) < 7 ? ((M >> SH) - 1) : 7;
+  static constexpr int B3 = (SH == 0 && R >= 16) ? SW : 0;
+  static __host__ __device__ __forceinline__ constexpr int swz(int r) {
+    return ((r & SW) ^ (((r >> 3) & 1) ? B3 : 0)) << SH;
+  }
   static __device__ __forceinline__ int idx(int li, int lj) {
     const int x = li >> RL, r = li & (R - 1);
     const int y = lj >> MLOG, c = lj & (M - 1);
-    return ((((x << H) | y) << RL | r) << MLOG) + (c ^ ((r & SW) << SH));
+    return ((((x << H) | y) << RL | r) << MLOG) + (c ^ swz(r));
   }
   // index of the partner whose row (or column) index has bit `pos` set, as
   // idx' = (idx + add) ^ xr, for an element whose index has that bit clear
   static __device__ __forceinline__ void row_delta(int pos, int& add, int& xr) {
-    if (pos < RL) { add = (1 << pos) << MLOG; xr = ((1 << pos) & SW) << SH; }
+    if (pos < RL) { add = (1 << pos) << MLOG; xr = swz(1 << pos); }
     else { add = (1 << (pos - RL)) << (H + RL + MLOG); xr = 0; }
   }
   static __device__ __forceinline__ void col_delta(int pos, int& add, int& xr) {
@@ -411,17 +422,24 @@ __device__ __forceinline__ void for_units(F&& unit) {
 template <class P, class G, int NT, int rows_log2g, int cols_log2g, bool ROLLED, int FORM>
 __device__ __forceinline__ void apply_1q_form(typename P::Elem* sm, const G& gm, const PassOp& op,
                                               const double* cf) {
-  constexpr int ncb_log2 = cols_log2g - 1;
-  constexpr int nb = 1 << (rows_log2g - 1 + ncb_log2);
+  constexpr int ncb_log2 = cols_log2g - 1, nrb_log2 = rows_log2g - 1;
+  constexpr int nb = 1 << (nrb_log2 + ncb_log2);
   constexpr int iters = (nb + NT - 1) / NT;
+  // where the bit-3 swizzle is on (16-byte elements, slots of >= 16 rows),
+  // consecutive threads take consecutive block rows of one block column,
+  // which is then conflict-free for every target bit; otherwise consecutive
+  // block columns of one block row
+  constexpr bool rows_first = G::B3 != 0;
   int ra, rx, ca, cx;
   gm.row_delta(op.rbit[0], ra, rx);
   gm.col_delta(op.cbit[0], ca, cx);
   for_units<iters, ROLLED>([&](int k) {
     const int b = int(threadIdx.x) + k * NT;
     if (nb % NT == 0 || b < nb) {
-      const int c0 = ins0i(b & ((1 << ncb_log2) - 1), op.cbit[0]);
-      const int r0 = ins0i(b >> ncb_log2, op.rbit[0]);
+      const int cb = rows_first ? b >> nrb_log2 : b & ((1 << ncb_log2) - 1);
+      const int rb = rows_first ? b & ((1 << nrb_log2) - 1) : b >> ncb_log2;
+      const int c0 = ins0i(cb, op.cbit[0]);
+      const int r0 = ins0i(rb, op.rbit[0]);
       const int i00 = gm.idx(r0, c0);
       const int i01 = (i00 + ca) ^ cx, i10 = (i00 + ra) ^ rx;
       const int i11 = (i10 + ca) ^ cx;
@@ -617,7 +635,6 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
   constexpr int rl = RL, R = 1 << RL;
   constexpr int slot_log2 = rl + m;
   constexpr int buf_elems = NSLOT << slot_log2;
-  constexpr int sw = G::SW;
   constexpr int rows_log2g = H + rl, cols_log2g = H + m;
   const int64_t chunk_mask = (int64_t(1) << d.chunks_log2) - 1;
   const int64_t tile_elems = int64_t(1) << (2 * m);
@@ -679,7 +696,7 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
           if (NG % kMainThreads == 0 || g < NG) {
             const int within = g << GSH;
             const int pr = within >> m, pc = within & (M - 1);
-            cp_async16(sbuf + (pr << m) + (pc ^ ((pr & sw) << GSH)), gbase + (r0 + pr) * M + pc);
+            cp_async16(sbuf + (pr << m) + (pc ^ G::swz(pr)), gbase + (r0 + pr) * M + pc);
           }
         }
       } else {
@@ -689,7 +706,7 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
           const int e = int(threadIdx.x) + k * kMainThreads;
           if (NE % kMainThreads == 0 || e < NE) {
             const int sr = e >> rl, sc = e & (R - 1);   // stored row / column (within the chunk)
-            cp_async_elem(sbuf + (sc << m) + (sr ^ ((sc & sw) << GSH)), gbase + sr * M + r0 + sc);
+            cp_async_elem(sbuf + (sc << m) + (sr ^ G::swz(sc)), gbase + sr * M + r0 + sc);
           }
         }
       }
@@ -760,7 +777,7 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
             const int within = g << GSH;
             const int pr = within >> m, pc = within & (M - 1);
             *reinterpret_cast<uint4*>(gbase + (r0 + pr) * M + pc) =
-                *reinterpret_cast<const uint4*>(sbuf + (pr << m) + (pc ^ ((pr & sw) << GSH)));
+                *reinterpret_cast<const uint4*>(sbuf + (pr << m) + (pc ^ G::swz(pr)));
           }
         }
       } else if (!diag) {
@@ -770,7 +787,7 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
           const int e = int(threadIdx.x) + k * kMainThreads;
           if (NE % kMainThreads == 0 || e < NE) {
             const int sr = e >> rl, sc = e & (R - 1);
-            gbase[sr * M + r0 + sc] = P::conj_if(sbuf[(sc << m) + (sr ^ ((sc & sw) << GSH))], 1u);
+            gbase[sr * M + r0 + sc] = P::conj_if(sbuf[(sc << m) + (sr ^ G::swz(sc))], 1u);
           }
         }
       }
