@@ -356,7 +356,9 @@ int orkan_pass_work(orkan_h h, double *alu_ops, double *bytes);
  * denominators of ALU and HBM rooflines): out[0] FP32 FMA, out[1] FP64 FMA,
  * out[2] FP32 add, out[3] FP64 add (instructions per second, each from 8
  * independent dependency chains per thread on 8 CTAs per SM), out[4] the read +
- * write bandwidth (GB/s) of a grid-stride copy of 16-byte elements.  scratch:
+ * write bandwidth (GB/s) of a grid-stride copy of 16-byte elements, out[5]
+ * paired FP32 FMA (f32x2) in lanes per second (two per instruction; 4 float2
+ * chains per thread, the same lane work as out[0]).  out holds 6 values.  scratch:
  * caller-owned device memory, at least 32 MiB (more gives a steadier copy
  * figure; 4 GiB is far beyond the L2).  Blocks for about a second; runs on the
  * legacy default stream.  Not part of any operation's path. */

@@ -35,6 +35,23 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_chain(T* sink, int iter
   if (s == T(-1.25)) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;   // never true; keeps the chains live
 }
 
+// Paired FP32 FMA (f32x2, one instruction for two lanes): CH / 2 chains of
+// float2 per thread, the same lane work per iteration as k_probe_chain<float>.
+__global__ void __launch_bounds__(kProbeThreads) k_probe_chain2(float* sink, int iters, float a, float b) {
+  float2 x[kChains / 2];
+#pragma unroll
+  for (int c = 0; c < kChains / 2; ++c) x[c] = make_float2(float(threadIdx.x) * 1e-3f + float(c), float(2 * c + 1));
+  const float2 aa = make_float2(a, a), bb = make_float2(b, b);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains / 2; ++c) x[c] = __ffma2_rn(x[c], aa, bb);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < kChains / 2; ++c) s += x[c].x + x[c].y;
+  if (s == -1.25f) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;   // never true; keeps the chains live
+}
+
 __global__ void k_probe_copy(const double2* __restrict__ src, double2* __restrict__ dst, int64_t n) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     dst[i] = src[i];
@@ -93,6 +110,8 @@ extern "C" int orkan_probe_pipes(double* out, void* scratch, size_t scratch_byte
                                        reinterpret_cast<float*>(sink), iters, 1.0f, 1e-9f); }, e0, e1, 3));
   out[3] = ops / (1e-3 * time_ms([&] { k_probe_chain<double, false><<<blocks, kProbeThreads>>>(
                                        sink, iters / 16, 1.0, 1e-9); }, e0, e1, 3)) / 16.0;
+  out[5] = ops / (1e-3 * time_ms([&] { k_probe_chain2<<<blocks, kProbeThreads>>>(
+                                       reinterpret_cast<float*>(sink), iters, 1.0000001f, 1e-9f); }, e0, e1, 3));
   cudaMemsetAsync(src, 0, size_t(n) * 16);
   out[4] = 2.0 * double(n) * 16.0 /
            (1e-3 * time_ms([&] { k_probe_copy<<<sms * 8, 512>>>(src, dst, n); }, e0, e1, 5)) / 1e9;

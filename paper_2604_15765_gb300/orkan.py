@@ -375,10 +375,10 @@ def orkan_expect_paulis_noalloc(dev_state: int, n: int, dtype: int, tile_log2: i
 
 def orkan_probe_pipes(scratch_ptr: int, scratch_bytes: int) -> dict:
     """Measured pipe rates (instructions/s) and copy bandwidth (GB/s) of the current GPU."""
-    out = (C.c_double * 5)()
+    out = (C.c_double * 6)()
     _check(_lib.orkan_probe_pipes(out, C.c_void_p(scratch_ptr), scratch_bytes), "orkan_probe_pipes")
     return {"fp32_fma_per_s": out[0], "fp64_fma_per_s": out[1], "fp32_add_per_s": out[2], "fp64_add_per_s": out[3],
-            "copy_GBps": out[4]}
+            "copy_GBps": out[4], "fp32x2_fma_lanes_per_s": out[5]}
 
 
 # ------------------------------------------------------------------ qubit relabelling
