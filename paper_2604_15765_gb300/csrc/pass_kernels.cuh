@@ -680,9 +680,40 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
   // Asynchronous loads of item w into stage buffer `buf`: rows of lower slots as
   // 16-byte granules; upper slots element by element into their transposed
   // (logical) place, reading the stored partner along its rows.
+  // 16-byte elements in slots smaller than the CTA (two high qubits at m = 5,
+  // and m <= 4): one flat walk over the item's elements, the slot's
+  // transposed bit selecting the shared and global addresses (a lower slot is
+  // read along its rows into place, an upper one along its stored rows into
+  // the transposed place).  A per-slot loop there leaves threads idle in every
+  // slot and branches per slot; with slots of at least kMainThreads elements
+  // the per-slot loop issues fewer instructions than the flat walk's selects.
+  constexpr bool FLAT = GSH == 0 && (1 << slot_log2) < kMainThreads;
+  constexpr int TOT = NSLOT << slot_log2;
+  constexpr int KF = (TOT + kMainThreads - 1) / kMainThreads;
+  auto flat = [&](int f, int& slot, int& srow, int& scol, int& goff, int r0, unsigned tm) {
+    slot = f >> slot_log2;
+    const int within = f & ((1 << slot_log2) - 1);
+    const bool t = (tm >> slot) & 1u;
+    srow = t ? (within & (R - 1)) : (within >> m);
+    scol = t ? (within >> rl) : (within & (M - 1));
+    goff = t ? (scol * M + r0 + srow) : ((r0 + srow) * M + scol);
+  };
   auto issue_loads = [&](int64_t w, int b, E* buf) {
     const int r0 = int(w & chunk_mask) << rl;
     const unsigned tm = s_tmask[b], vm = s_vmask[b];
+    if constexpr (FLAT) {
+#pragma unroll
+      for (int k = 0; k < KF; ++k) {
+        const int f = int(threadIdx.x) + k * kMainThreads;
+        if (TOT % kMainThreads == 0 || f < TOT) {
+          int slot, srow, scol, goff;
+          flat(f, slot, srow, scol, goff, r0, tm);
+          if ((vm >> slot) & 1u)
+            cp_async16(buf + (slot << slot_log2) + (srow << m) + (scol ^ G::swz(srow)), st + s_base[b][slot] + goff);
+        }
+      }
+      return;
+    }
 #pragma unroll 1
     for (int slot = 0; slot < NSLOT; ++slot) {
       if (!((vm >> slot) & 1u)) continue;
@@ -738,6 +769,13 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
 
     const unsigned tm = s_tmask[ii], vm = s_vmask[ii];
     if (tm) {   // upper slots arrive transposed but not yet conjugated
+      if constexpr (FLAT) {
+#pragma unroll
+        for (int k = 0; k < KF; ++k) {
+          const int f = int(threadIdx.x) + k * kMainThreads;
+          if ((TOT % kMainThreads == 0 || f < TOT) && ((tm >> (f >> slot_log2)) & 1u)) sm[f] = P::conj_if(sm[f], 1u);
+        }
+      } else {
 #pragma unroll 1
       for (int slot = 0; slot < NSLOT; ++slot) {
         if (!((tm >> slot) & 1u)) continue;
@@ -747,6 +785,7 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
           const int e = int(threadIdx.x) + k * kMainThreads;
           if ((1 << slot_log2) % kMainThreads == 0 || e < (1 << slot_log2)) sbuf[e] = P::conj_if(sbuf[e], 1u);
         }
+      }
       }
       __syncthreads();
     }
@@ -763,6 +802,23 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
     // a diagonal group, where they mirror lower slots of the same group)
     const int r0 = int(w & chunk_mask) << rl;
     const bool diag = s_diag[ii];
+    if constexpr (FLAT) {
+      // an upper slot goes back conjugated into its stored partner, except in
+      // a diagonal group (there it mirrors a lower slot of the same group)
+      const unsigned wm = vm & (diag ? ~tm : ~0u);
+#pragma unroll
+      for (int k = 0; k < KF; ++k) {
+        const int f = int(threadIdx.x) + k * kMainThreads;
+        if (TOT % kMainThreads == 0 || f < TOT) {
+          int slot, srow, scol, goff;
+          flat(f, slot, srow, scol, goff, r0, tm);
+          if ((wm >> slot) & 1u)
+            st[s_base[ii][slot] + goff] =
+                P::conj_if(sm[(slot << slot_log2) + (srow << m) + (scol ^ G::swz(srow))], (tm >> slot) & 1u);
+        }
+      }
+      continue;
+    }
 #pragma unroll 1
     for (int slot = 0; slot < NSLOT; ++slot) {
       if (!((vm >> slot) & 1u)) continue;
