@@ -688,6 +688,13 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
   // slot and branches per slot; with slots of at least kMainThreads elements
   // the per-slot loop issues fewer instructions than the flat walk's selects.
   constexpr bool FLAT = GSH == 0 && (1 << slot_log2) < kMainThreads;
+  // 8-byte elements: the same flat walk over 16-byte granules for items whose
+  // slots are all lower (every item of a row-chunked pass, whose diagonal
+  // groups run in pass_kernel_diag), when a slot has fewer granules than the CTA
+  constexpr int GSL = slot_log2 - GSH;   // log2 granules per slot
+  constexpr bool FLATG = GSH == 1 && (1 << GSL) < kMainThreads;
+  constexpr int TOTG = NSLOT << GSL;
+  constexpr int KG = (TOTG + kMainThreads - 1) / kMainThreads;
   constexpr int TOT = NSLOT << slot_log2;
   constexpr int KF = (TOT + kMainThreads - 1) / kMainThreads;
   auto flat = [&](int f, int& slot, int& srow, int& scol, int& goff, int r0, unsigned tm) {
@@ -713,6 +720,21 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
         }
       }
       return;
+    }
+    if constexpr (FLATG) {
+      if (tm == 0u) {
+#pragma unroll
+        for (int k = 0; k < KG; ++k) {
+          const int g = int(threadIdx.x) + k * kMainThreads;
+          if (TOTG % kMainThreads == 0 || g < TOTG) {
+            const int slot = g >> GSL, within = (g & ((1 << GSL) - 1)) << GSH;
+            const int pr = within >> m, pc = within & (M - 1);
+            if ((vm >> slot) & 1u)
+              cp_async16(buf + (slot << slot_log2) + (pr << m) + (pc ^ G::swz(pr)), st + s_base[b][slot] + (r0 + pr) * M + pc);
+          }
+        }
+        return;
+      }
     }
 #pragma unroll 1
     for (int slot = 0; slot < NSLOT; ++slot) {
@@ -818,6 +840,22 @@ pass_kernel(typename P::Elem* __restrict__ st, const __grid_constant__ PassDesc 
         }
       }
       continue;
+    }
+    if constexpr (FLATG) {
+      if (tm == 0u) {
+#pragma unroll
+        for (int k = 0; k < KG; ++k) {
+          const int g = int(threadIdx.x) + k * kMainThreads;
+          if (TOTG % kMainThreads == 0 || g < TOTG) {
+            const int slot = g >> GSL, within = (g & ((1 << GSL) - 1)) << GSH;
+            const int pr = within >> m, pc = within & (M - 1);
+            if ((vm >> slot) & 1u)
+              *reinterpret_cast<uint4*>(st + s_base[ii][slot] + (r0 + pr) * M + pc) =
+                  *reinterpret_cast<const uint4*>(sm + (slot << slot_log2) + (pr << m) + (pc ^ G::swz(pr)));
+          }
+        }
+        continue;
+      }
     }
 #pragma unroll 1
     for (int slot = 0; slot < NSLOT; ++slot) {
