@@ -853,28 +853,38 @@ def main(argv=None):
     ok.orkan_store_tiled(runner.rho, host_rho.numpy())
     ok.orkan_store_tiled(runner.O, host_O.numpy())
     e2e_steps = max(2, args.steps // 2)
-
-    phase = {"upload_s": 0.0, "step_s": 0.0}
+    # Each step queues both uploads without waiting: the observable has its
+    # own stream, so its copy (and its passes) overlap the state's passes;
+    # the state's passes follow its copy on its stream, and tr(rho O) waits
+    # for the observable's stream.  Copy durations are timed with events on
+    # the copies' own streams.
+    stream_o = torch.cuda.Stream()
+    ok.orkan_set_stream(runner.O, stream_o.cuda_stream)
+    s_rho = torch.cuda.current_stream()   # the state's stream (the runner's `stream`)
+    copy_ev = []
 
     def e2e_step():
-        ta = time.perf_counter()
-        ok.orkan_load_tiled(runner.rho, host_rho.numpy(), ok.ORKAN_STATE)
-        ok.orkan_load_tiled(runner.O, host_O.numpy(), ok.ORKAN_OBSERVABLE)   # both return after their copies
-        tb = time.perf_counter()
-        res = runner.step()                                                  # ends with blocking readouts
-        phase["upload_s"] += tb - ta
-        phase["step_s"] += time.perf_counter() - tb
-        return res
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(s_rho)
+        ok.orkan_load_tiled_async(runner.rho, host_rho.numpy(), ok.ORKAN_STATE)
+        ev[1].record(s_rho)
+        ev[2].record(stream_o)
+        ok.orkan_load_tiled_async(runner.O, host_O.numpy(), ok.ORKAN_OBSERVABLE)
+        ev[3].record(stream_o)
+        copy_ev.append(ev)
+        return runner.step()                                                 # ends with blocking readouts
 
     e2e_step()
     torch.cuda.synchronize()
     barrier()
-    phase.update(upload_s=0.0, step_s=0.0)
+    copy_ev.clear()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    upload_ms = sum(ev[0].elapsed_time(ev[1]) + ev[2].elapsed_time(ev[3]) for ev in copy_ev) / e2e_steps
+    ok.orkan_set_stream(runner.O, stream)
     e2e_units, e2e_tot = aggregate(runner.ops_per_step * e2e_steps, e2e_s)
     op_bytes = sum(16 * op["matrix"].size if op["kind"] == "unitary" else 8 for op in wl["ops"]) * 2
     h2d = 2 * runner.bytes + op_bytes
@@ -946,8 +956,9 @@ def main(argv=None):
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_units / e2e_tot, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "host_cores_near_gpu": bound_cores,
-                    "upload_ms_per_step": round(1e3 * phase["upload_s"] / e2e_steps, 2),
-                    "compute_ms_per_step": round(1e3 * phase["step_s"] / e2e_steps, 2)},
+                    "upload_ms_per_step": round(upload_ms, 2),
+                    "ms_per_step": round(1e3 * e2e_s / e2e_steps, 2),
+                    "uploads": "asynchronous from pinned memory; the observable's copy overlaps the state's passes"},
             "gpu_launches": launches,
             "clocks": clocks,
             "variants": variants,

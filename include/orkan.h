@@ -179,6 +179,16 @@ int orkan_set_picture(orkan_h h, int picture);
 int orkan_load_tiled(orkan_h h, const void *host_src, int picture);
 int orkan_store_tiled(orkan_h h, void *host_dst);
 
+/* orkan_load_tiled without the wait: the copy is queued on the handle's
+ * stream and the call returns.  Later calls on h are ordered after the copy;
+ * host_src must stay valid and unchanged until it has completed (after
+ * orkan_sync(h) or any blocking call on h).  From pinned host memory the copy
+ * runs asynchronously, so an upload to one handle can overlap the passes of
+ * a handle on another stream; from pageable memory the driver may finish it
+ * before returning.  Host-device plumbing with no counterpart in the paper.
+ * Errors: EINVAL (NULL host_src, bad picture, during graph capture), ECUDA. */
+int orkan_load_tiled_async(orkan_h h, const void *host_src, int picture);
+
 /* ------------------------------------------------------------------ operations
  * On a STATE handle these apply Phi (Eq. 1); on an OBSERVABLE handle Phi*
  * (the caller issues a circuit's ops in reverse order for Heisenberg

@@ -1066,6 +1066,16 @@ int orkan_load_tiled(orkan_h h, const void* host_src, int picture) {
   return ORKAN_OK;
 }
 
+int orkan_load_tiled_async(orkan_h h, const void* host_src, int picture) {
+  if (int st = check_blocking(h)) return st;
+  if (!host_src || (picture != ORKAN_STATE && picture != ORKAN_OBSERVABLE)) return fail(ORKAN_EINVAL, "bad args");
+  h->pending.clear();
+  reset_labels(h);
+  h->picture = picture;
+  ORKAN_CUDA(cudaMemcpyAsync(h->d_state, host_src, h->bytes, cudaMemcpyHostToDevice, h->stream));
+  return ORKAN_OK;
+}
+
 int orkan_store_tiled(orkan_h h, void* host_dst) {
   if (int st = check_blocking(h)) return st;
   if (!host_dst) return fail(ORKAN_EINVAL, "null destination");

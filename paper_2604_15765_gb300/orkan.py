@@ -69,6 +69,7 @@ _SIGS = {
     "orkan_set_picture": (C.c_int, [_h, C.c_int]),
     "orkan_load_tiled": (C.c_int, [_h, C.c_void_p, C.c_int]),
     "orkan_store_tiled": (C.c_int, [_h, C.c_void_p]),
+    "orkan_load_tiled_async": (C.c_int, [_h, C.c_void_p, C.c_int]),
     "orkan_apply_unitary": (C.c_int, [_h, C.c_int, _pi, _pd]),
     "orkan_apply_kraus": (C.c_int, [_h, C.c_int, _pi, C.c_int, _pd]),
     "orkan_depolarize": (C.c_int, [_h, C.c_int, C.c_double]),
@@ -228,6 +229,14 @@ def orkan_set_picture(h, picture: int):
 def orkan_load_tiled(h, host_buf: np.ndarray, picture: int = ORKAN_STATE):
     buf = np.ascontiguousarray(host_buf)
     _check(_lib.orkan_load_tiled(h, buf.ctypes.data_as(C.c_void_p), picture), "orkan_load_tiled")
+
+
+def orkan_load_tiled_async(h, host_buf: np.ndarray, picture: int = ORKAN_STATE):
+    """Queue the raw tiled upload on the handle's stream and return; host_buf
+    (C-contiguous, ideally pinned) must stay alive and unchanged until the copy
+    completes (orkan_sync or any blocking call on h)."""
+    assert host_buf.flags["C_CONTIGUOUS"]
+    _check(_lib.orkan_load_tiled_async(h, host_buf.ctypes.data_as(C.c_void_p), picture), "orkan_load_tiled_async")
 
 
 def orkan_store_tiled(h, host_buf: np.ndarray):
