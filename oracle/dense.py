@@ -206,7 +206,9 @@ def measure(H, q, u):
 
 
 def project(H, q, b):
-    """Pi_b H Pi_b without renormalisation (self-adjoint, so both pictures)."""
+    """Pi_b H Pi_b without renormalisation: the single-Kraus trace
+    non-increasing map of Sec. II with K = Pi_b, which is self-adjoint, so
+    both pictures apply the same map."""
     return apply_kraus(H, [projector(b)], [q])
 
 
@@ -222,6 +224,8 @@ def pauli_matrix(pauli: str) -> np.ndarray:
 
 
 def pauli_sum(paulis, coeffs) -> np.ndarray:
+    """O = sum_t coeffs[t] P_t, the observable evolved in the Heisenberg
+    picture (Sec. I: predictions tr(rho O) are the same in both pictures)."""
     n = len(paulis[0])
     O = np.zeros((1 << n, 1 << n), dtype=np.complex128)
     for s, c in zip(paulis, coeffs):

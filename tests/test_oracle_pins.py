@@ -367,6 +367,86 @@ def test_pauli_y_eigenstate():
     assert D.expect_pauli(rho, "YZ") == pytest.approx(0.0)
 
 
+_SIGMA = {
+    "I": ((1, 0), (0, 1)),
+    "X": ((0, 1), (1, 0)),
+    "Y": ((0, -1j), (1j, 0)),
+    "Z": ((1, 0), (0, -1)),
+}
+
+
+def _pauli_element(pauli, i, j):
+    """<i|P|j> = prod_l sigma_{pauli[l]}[bit l of i, bit l of j], from the
+    definition of a tensor product of single-qubit Paulis (character l on
+    qubit l), without any Kronecker product."""
+    v = 1.0 + 0j
+    for l, ch in enumerate(pauli):
+        v *= _SIGMA[ch][(i >> l) & 1][(j >> l) & 1]
+    return v
+
+
+def test_pauli_sum_coefficients():
+    """O = sum_a c_a P_a (the observable of the Heisenberg workloads): the
+    Pauli strings are orthogonal, tr(P_a P_b) = N delta_ab, so
+    tr(P_a O) / N = c_a for distinct strings and 0 for a string not in the
+    sum.  A single term c P has the eigenvalues +c and -c, N / 2 times each."""
+    rng = S.rng_for(410)
+    n = 3
+    N = 1 << n
+    strings = ["XIZ", "YYI", "IZX", "ZXY", "III"]
+    coeffs = rng.standard_normal(len(strings))
+    O = D.pauli_sum(strings, coeffs)
+    for s, c in list(zip(strings, coeffs)) + [("XXX", 0.0), ("IIZ", 0.0)]:
+        tr = sum(_pauli_element(s, j, i) * O[i, j] for i in range(N) for j in range(N))
+        assert tr / N == pytest.approx(c, abs=1e-13)
+    for s in ("XIZ", "ZYX", "IIY"):
+        ev = np.sort(np.linalg.eigvalsh(D.pauli_sum([s], [-1.75])))
+        assert np.max(np.abs(ev - np.repeat([-1.75, 1.75], N // 2))) < 1e-14
+
+
+def test_project_keeps_only_the_outcome_block():
+    """Pi_b H Pi_b (Sec. II, a trace non-increasing map): every element whose
+    row or column has bit q != b becomes 0, the rest are unchanged; a state
+    with qubit q in |b'> projects to 0 for b' != b and is left as it is for
+    b' = b; and measure() equals project() divided by p_b."""
+    rng = S.rng_for(420)
+    n = 3
+    N = 1 << n
+    H = S.random_hermitian(rng, N)
+    for q in range(n):
+        for b in (0, 1):
+            got = D.project(H, q, b)
+            for i in range(N):
+                for j in range(N):
+                    keep = ((i >> q) & 1) == b and ((j >> q) & 1) == b
+                    assert got[i, j] == (H[i, j] if keep else 0)
+    rest = S.ginibre_state(rng, 1 << (n - 1))
+    for q in range(n):
+        for bp in (0, 1):
+            e = np.zeros((2, 2), dtype=np.complex128)
+            e[bp, bp] = 1
+            # qubit q in |bp>, the other qubits in the state ``rest``
+            full = np.zeros((N, N), dtype=np.complex128)
+            others = [x for x in range(n) if x != q]
+            for i in range(N):
+                for j in range(N):
+                    ri = sum(((i >> x) & 1) << t for t, x in enumerate(others))
+                    rj = sum(((j >> x) & 1) << t for t, x in enumerate(others))
+                    full[i, j] = e[(i >> q) & 1, (j >> q) & 1] * rest[ri, rj]
+            for b in (0, 1):
+                got = D.project(full, q, b)
+                if b == bp:
+                    assert np.array_equal(got, full)
+                else:
+                    assert not np.any(got)
+    rho = S.ginibre_state(rng, N)
+    for q in range(n):
+        for u in (0.2, 0.8):
+            post, b, _ = D.measure(rho, q, u)
+            pb = D.born_probabilities(rho, q)[b]
+            assert np.max(np.abs(post - D.project(rho, q, b) / pb)) < 1e-15
+
+
 def test_tiled_mean_value_equals_trace():
     rng = S.rng_for(400)
     for n, m in ((3, 1), (5, 2), (6, 5), (2, 5), (6, 3)):
@@ -416,6 +496,23 @@ def test_planted_mistakes_are_caught(monkeypatch):
         mp.setattr(D, "embed", lambda L, q, n, sparse=None: orig_embed(L, [n - 1 - x for x in q], n, sparse))
         with pytest.raises(AssertionError):
             test_bell_amplitude_damping()
+    # 6) swapped coefficients in the Pauli sum
+    orig_sum = D.pauli_sum
+    with monkeypatch.context() as mp:
+        mp.setattr(D, "pauli_sum", lambda s, c: orig_sum(s, list(c)[::-1]))
+        with pytest.raises(AssertionError):
+            test_pauli_sum_coefficients()
+    # 7) a dropped term in the Pauli sum
+    with monkeypatch.context() as mp:
+        mp.setattr(D, "pauli_sum", lambda s, c: orig_sum(s[:-1], list(c)[:-1]))
+        with pytest.raises(AssertionError):
+            test_pauli_sum_coefficients()
+    # 8) the projector onto the other outcome
+    orig_proj = D.projector
+    with monkeypatch.context() as mp:
+        mp.setattr(D, "project", lambda H, q, b: D.apply_kraus(H, [orig_proj(1 - b)], [q]))
+        with pytest.raises(AssertionError):
+            test_project_keeps_only_the_outcome_block()
 
 
 def test_factored_kraus_matches_dense():
