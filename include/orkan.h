@@ -116,7 +116,8 @@ int orkan_ptm(int k, int r, const double *K, int adjoint, double *out);
 
 /* ------------------------------------------------------------------ lifetime */
 
-/* Allocate an n-qubit operator (1 <= n <= 24) with tile edge 2^tile_log2
+/* Storage of Sec. III-B (tiled lower triangle, Table I footprint).
+ * Allocate an n-qubit operator (1 <= n <= 24) with tile edge 2^tile_log2
  * (3 <= tile_log2 <= 5; the paper's m = 5 is the default when tile_log2 is 0)
  * on the current CUDA device.  The content is undefined until an init call.
  * Errors: EINVAL, ENOMEM, ENODEV, ECUDA. */
@@ -126,7 +127,8 @@ int orkan_alloc(int n, int dtype, int tile_log2, orkan_h *out);
  * 256-byte aligned (e.g. a torch tensor); orkan_free does not release it. */
 int orkan_alloc_external(int n, int dtype, int tile_log2, void *dev_ptr, size_t bytes, orkan_h *out);
 
-/* Wait for the handle's work and release it (and its memory unless external). */
+/* Sec. III-B storage lifetime.
+ * Wait for the handle's work and release it (and its memory unless external). */
 int orkan_free(orkan_h h);
 
 /* Run the handle's work on the given cudaStream_t (NULL = the legacy default
@@ -159,11 +161,13 @@ void *orkan_device_ptr(orkan_h h);
 
 /* ------------------------------------------------------------------ initialisation */
 
-/* Set the handle to a state (picture ORKAN_STATE).  See ORKAN_INIT_*.
+/* Sec. III-B layout, Sec. II (a state is the hermitian H that Phi acts on).
+ * Set the handle to a state (picture ORKAN_STATE).  See ORKAN_INIT_*.
  * Errors: EINVAL (unknown kind, NULL data for DENSE/PURE), ENOMEM, ECUDA. */
 int orkan_init_state(orkan_h h, int kind, const double *data);
 
-/* Set the handle to the observable O = sum_t coeffs[t] P_t (picture
+/* Sec. I / Sec. II trace duality: the observable is the operand of the
+ * Heisenberg picture.  Set the handle to the observable O = sum_t coeffs[t] P_t (picture
  * ORKAN_OBSERVABLE).  paulis: nterms strings of n characters from "IXYZ"
  * back to back (no separators); character l acts on qubit l.
  * Errors: EINVAL (bad character, nterms < 0), ENOMEM, ECUDA. */
@@ -214,7 +218,11 @@ int orkan_dephase(orkan_h h, int q, double p);
 /* Amplitude damping: diag(1, sqrt(1-gamma)), sqrt(gamma)|0><1|.  Not defined in the paper. */
 int orkan_amplitude_damp(orkan_h h, int q, double gamma);
 
-/* Z-basis measurement of qubit q on a STATE handle with the caller's uniform
+/* Sec. II: the projectors Pi_0, Pi_1 form a CP trace non-increasing map;
+ * Born renormalisation is not in the paper (it mentions only trace
+ * non-increasing maps), so the reading here is p_b = tr(Pi_b rho) and
+ * rho <- Pi_b rho Pi_b / p_b.
+ * Z-basis measurement of qubit q on a STATE handle with the caller's uniform
  * draw u in [0, 1): p_b = tr(Pi_b rho) in FP64, outcome = 0 iff
  * u (p0 + p1) < p0, then rho <- Pi_b rho Pi_b / p_b (Born renormalisation).
  * *outcome and *prob (= p_b / (p0 + p1)) are written on success.
@@ -222,7 +230,8 @@ int orkan_amplitude_damp(orkan_h h, int q, double gamma);
  * Errors: EPICTURE on an observable, EZEROPROB, EINVAL. */
 int orkan_measure(orkan_h h, int q, double u, int *outcome, double *prob);
 
-/* Pi_b H Pi_b without renormalisation (both pictures). */
+/* Sec. II (CP trace non-increasing map with the single Kraus operator
+ * Pi_b, self-adjoint): Pi_b H Pi_b without renormalisation (both pictures). */
 int orkan_project(orkan_h h, int q, int outcome);
 
 /* ------------------------------------------------------------------ whole circuits in one call */
@@ -254,17 +263,21 @@ int orkan_run_circuit(orkan_h h, int count, const orkan_op *ops, int *outcomes, 
 
 /* ------------------------------------------------------------------ readouts (block; FP64) */
 
-/* tr H = sum_i H_ii (re, im). */
+/* Sec. III-C (the diagonal of the diagonal tiles): tr H = sum_i H_ii (re, im). */
 int orkan_trace(orkan_h h, double *re, double *im);
 
-/* tr(P H) for the Pauli string P (n characters of "IXYZ", character l on qubit l). */
+/* Sec. I / Sec. III-C mean value tr(rho O) with O a Pauli string: tr(P H)
+ * for P given as n characters of "IXYZ", character l on (logical) qubit l;
+ * reads the N elements H[i ^ x, i] (x = the string's X/Y mask). */
 int orkan_expect_pauli(orkan_h h, const char *pauli, double *out);
 
 /* tr(rho O) as tiled Frobenius products (Sec. III-C; diagonal tiles once,
  * strictly lower tiles twice).  Both handles: same n, tile size and dtype. */
 int orkan_expect(orkan_h rho, orkan_h O, double *out);
 
-/* Dense N x N complex128 row-major copy into host memory out (2 N^2 doubles).
+/* Sec. III-B (the inverse of the tiled map, upper tiles mirrored from the
+ * stored lower ones).
+ * Dense N x N complex128 row-major copy into host memory out (2 N^2 doubles).
  * Elements above the diagonal are conjugates of the stored lower ones. */
 int orkan_to_dense(orkan_h h, double *out);
 
@@ -383,11 +396,21 @@ int orkan_probe_pipes(double *out, void *scratch, size_t scratch_bytes);
  * pointer of a tiled operator.
  *
  * tr(P_s H) for count Pauli strings P_s (count * n characters of "IXYZ" back
- * to back, character l on qubit l), read from the tiled array at dev_state
- * (caller-owned device memory: n qubits, dtype, tile_log2 as for orkan_alloc,
- * layout of Sec. III-B, with any pending fused ops of its handle already
- * flushed).  The results go to the host array out[count].  Work is issued on
- * cuda_stream (NULL = legacy default stream) and the call returns after it.
+ * to back).  dev_state is caller-owned device memory holding the array that
+ * orkan_device_ptr returns for a handle of this n, dtype and tile_log2, and
+ * the strings act on that array's bit positions: character l acts on
+ * physical bit position l.  For a handle whose labels are not the identity
+ * (orkan_relabel, or the automatic planner), move character q of a logical
+ * string to position phys[q] (orkan_get_labels) first.
+ *
+ * Ordering: the call reads dev_state on cuda_stream (NULL = legacy default
+ * stream).  Every write to dev_state must have completed before, or be
+ * ordered before cuda_stream by the caller: a handle's stream is a
+ * non-blocking stream, so work flushed to it is NOT ordered before the
+ * legacy default stream or any other stream.  Either call orkan_sync on the
+ * handle first, or record an event on the handle's stream and make
+ * cuda_stream wait for it.  The results go to the host array out[count];
+ * the call returns after its work on cuda_stream has finished.
  *
  * Scratch: no cudaMalloc / cudaFree or other allocating routine is called.  The
  * partial sums live in one fixed, file-scope device array of
@@ -399,10 +422,13 @@ int orkan_probe_pipes(double *out, void *scratch, size_t scratch_bytes);
  * reads, so nothing needs clearing, but calls whose work overlaps on the GPU
  * (other host threads, other streams) race on it and must be serialised by the
  * caller.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) once, with that device current; make that first call
- * before any stream capture.
+ * (cudaGetSymbolAddress) once, with that device current, and keeps it for the
+ * life of the process; make that first call before any stream capture.  The
+ * kept address does not survive cudaDeviceReset: do not call this entry
+ * point on a device after resetting it.
  *
- * Results equal orkan_expect_pauli's bit for bit (same reduction order).
+ * Results equal orkan_expect_pauli's bit for bit for the same string (same
+ * grid, per-thread order and reduction tree).
  * Errors: EINVAL (null pointers, bad n / dtype / tile_log2, count out of
  * range, bad character), ECUDA. */
 #define ORKAN_NOALLOC_MAX_STRINGS 64

@@ -14,7 +14,9 @@
 // The kernels are a batched copy of the library's Pauli-expectation
 // reduction: a fixed grid of kRedBlocks CTAs per string, FP64 accumulation,
 // the same per-thread order, shuffle tree and single-CTA final pass, so the
-// results equal those of orkan_expect_pauli bit for bit.
+// results equal those of orkan_expect_pauli bit for bit.  The entry point
+// sees only a device array, not a handle, so it knows no qubit labels:
+// character l of a string acts on physical bit position l of the array.
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -103,7 +105,9 @@ __global__ void k_na_finalize(double* scratch) {
   na_block_sum2(v0, v1, scratch + kNaPartials + 2 * size_t(s));
 }
 
-// Device address of g_noalloc_scratch, looked up once per device.
+// Device address of g_noalloc_scratch, looked up once per device (with that
+// device current) and kept for the process; it does not survive a
+// cudaDeviceReset of that device.
 constexpr int kMaxDevices = 64;
 std::mutex g_na_mutex;
 double* g_na_ptr[kMaxDevices] = {};
