@@ -14,7 +14,14 @@ is one pass of the whole hot path:
   reverse order, then tr(rho O) from the tiled Frobenius products.
 
 value = k-local ops (2 x 70 + 1 measurement per step) / device time, with the
-operands resident in HBM and continuously evolved (as in Sec. IV-A).  e2e
+operands resident in HBM and continuously evolved (as in Sec. IV-A), in
+native FP64 arithmetic on complex128 storage (the paper's precision) unless
+--dtype names another form.  The roofline is on the HBM basis (2 x stored
+bytes per pass / average pass time / measured copy bandwidth) with the FP64
+pipe's share of its derived peak beside it.  The line also carries the
+first layers of the n = 16 noisy brickwork in FP64, the plain one-op-per-pass
+FP64 path and the double-float and complex64 forms with their errors against
+the FP64 run, single-op pass bandwidths, and a served sample with p50/p99.  e2e
 repeats the step through the same C ABI with the operands uploaded from
 pinned host memory every step and the scalars read back.  Under torchrun each
 rank runs an independent replica (weak scaling, no collective on the data
@@ -48,7 +55,7 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["orkan", "reference"], default="orkan")
-    p.add_argument("--dtype", choices=list(DTYPE_NAMES), default="df64")
+    p.add_argument("--dtype", choices=list(DTYPE_NAMES), default="c128")
     p.add_argument("--n", type=int, default=14)
     p.add_argument("--tile-log2", type=int, default=5)
     p.add_argument("--fusion", type=int, default=8)
@@ -59,6 +66,8 @@ def parse_args(argv=None):
     p.add_argument("--workload", choices=["sweep", "serving", "brickwork", "precision", "paper", "relabel", "pipes"],
                    default="sweep")
     p.add_argument("--depth", type=int, default=40)
+    p.add_argument("--bw-depth", type=int, default=6,
+                   help="layers of the n=16 noisy brickwork timed in the default run (0 = skip)")
     p.add_argument("--serve-requests", type=int, default=160,
                    help="requests in the serving sample of the default run (the serving workload uses 5000)")
     p.add_argument("--paper-sizes", default="6,8,10,12,13,14,15,16", help="qubit counts of the paper study")
@@ -214,10 +223,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# ALU peaks of GB300: 152 SMs at the 2070 MHz maximum clock, with per-SM rates measured on GB300 by an
-# FMA-chain probe: FP32 pipe 128 lane-ops per clock per SM, FP64 pipe 2 per clock per SM.
-ALU_PEAK_TOPS = {"df64": 152 * 128 * 2.07e9 / 1e12, "c64": 152 * 128 * 2.07e9 / 1e12,
-                 "c128": 152 * 2.0 * 2.07e9 / 1e12}
+# Derived ALU peaks: the device's SM count x the pipe's unit rate per SM per clock x the 2070 MHz maximum
+# SM clock.  Unit rates: FP32 128 lanes (4 x 32 FP32 units; the pipe probe measures 119-125), FP64 2 operations
+# (the pipe probe measures 1.97 FMA per SM per clock on GB300).
+UNIT_RATE = {"df64": 128.0, "c64": 128.0, "c128": 2.0}
+SM_MAX_HZ = 2.07e9
+
+
+def alu_peak_tops(dtype: str, sms: int) -> float:
+    return sms * UNIT_RATE[dtype] * SM_MAX_HZ / 1e12
 
 
 def traffic_record(dtype: str):
@@ -362,62 +376,102 @@ def per_op_table(ok, wl, n, m, dtypes, stream, torch, reps=4, only=None):
     return out
 
 
+def _request_errors(reqs, res, ref):
+    """Largest |result - reference| per request dtype (c128 / c64 requests)."""
+    out = {}
+    for dt in ("c128", "c64"):
+        d = [float(np.max(np.abs(np.asarray(res[r["id"]]) - np.asarray(ref[r["id"]])))) for r in reqs
+             if r["dtype"] == dt and r["id"] in res and r["id"] in ref]
+        out[f"max_abs_err_{dt}_requests"] = max(d) if d else None
+    return out
+
+
 def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=True):
     """Continuous batching vs one-at-a-time plain FP64 on the same requests.
+    The plain arm runs every request alone, one pass per op, in native FP64
+    (c64 requests too); its results are the reference for every served arm's
+    per-request error.  Served arms: requests at their own dtype (c128 in
+    native FP64, c64 in FP32) and, separately, c128 requests in double-float.
     Capacity: all requests present at t = 0; latency runs: Poisson arrivals at
     a fraction of the measured capacity (arrival times rescaled), served in
     arrival order (fifo) and shortest-estimated-work first (sjf)."""
     from paper_2604_15765_gb300 import serving
-    served_map = {"c128": "df64"}
     out = {"requests": len(reqs), "slots": slots, "memory_budget_bytes": budget,
-           "served_form": "8 concurrent slots, c128 requests in df64, fused passes (8 ops, composed)"}
-    _, cap = serving.serve(reqs, budget, slots=slots, dtype_map=served_map, realtime=False)
+           "served_form": "8 concurrent slots, fused passes (8 ops, composed)"}
+    ref = None
+    if baseline:
+        ref, b = serving.serve(reqs, budget, slots=1, dtype_map={"c64": "c128"}, fusion=1, compose=False,
+                               realtime=False)
+        out["plain_fp64_one_at_a_time"] = b
+    arms = (("c128", {}), ("df64", {"c128": "df64"}))
+    cap = None
+    for label, dmap in arms:
+        res, st = serving.serve(reqs, budget, slots=slots, dtype_map=dmap, realtime=False)
+        st["c128_requests_in"] = label
+        if ref is not None:
+            st.update(_request_errors(reqs, res, ref))
+        out[f"served_capacity_{label}"] = st
+        if cap is None:
+            cap = st
     out["served_capacity"] = cap
     base_t = [r["t"] for r in reqs]
     for frac in realtime_fracs:
         rate = frac * cap["solves_per_s"]
         span = base_t[-1] if base_t[-1] > 0 else 1.0
         scaled = [dict(r, t=r["t"] * (len(reqs) / rate) / span) for r in reqs]
-        _, st = serving.serve(scaled, budget, slots=slots, dtype_map=served_map, realtime=True)
+        _, st = serving.serve(scaled, budget, slots=slots, realtime=True)
         out[f"served_at_{frac:.1f}x_capacity"] = st
-        _, st = serving.serve(scaled, budget, slots=slots, dtype_map=served_map, realtime=True, policy="sjf")
+        _, st = serving.serve(scaled, budget, slots=slots, realtime=True, policy="sjf")
         out[f"served_at_{frac:.1f}x_capacity_sjf"] = st
-    if baseline:
-        _, b = serving.serve(reqs, budget, slots=1, dtype_map={"c64": "c128"}, fusion=1, compose=False,
-                             realtime=False)
-        out["plain_fp64_one_at_a_time"] = b
     torch.cuda.synchronize()
     return out
 
 
-def _run_timed(ok, circuit, torch, stream, n, dt, m, fusion, compose, ops, paulis, psi):
-    """One operator through ops, then the Pauli strings; device time, pass stats, handle."""
+def sweep_elements(ok, circuit, wl, n, m, dt, fusion, compose, stream, sample=None):
+    """One Schroedinger sweep from the bench's initial state (the Haar pure
+    state depolarised on every qubit) in the given form; returns sampled
+    elements (complex128) and the sample (rows, cols, diagonal count)."""
     h = ok.orkan_alloc(n, DTYPE_NAMES[dt], m)
     ok.orkan_set_stream(h, stream)
     ok.orkan_set_fusion(h, fusion, compose)
-    ok.orkan_init_state(h, ok.ORKAN_INIT_PURE, psi)
-    ok.orkan_sync(h)
-    ok.orkan_set_timing(h, True)
-    ok.orkan_pass_time(h)
-    p0 = ok.orkan_stats(h)["passes"]
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for op in ops:
-        circuit.apply_op(h, op)
-    ok.orkan_flush(h)
-    ev1.record()
-    exps = np.array([ok.orkan_expect_pauli(h, s) for s in paulis])
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    pass_ms, cnt = ok.orkan_pass_time(h)
-    ok.orkan_set_timing(h, False)
-    nb = 2 * ok.orkan_bytes(n, DTYPE_NAMES[dt], m)
-    st = {"ops_per_s": round(len(ops) / (ms / 1e3), 1), "ms": round(ms, 1), "passes": ok.orkan_stats(h)["passes"] - p0,
-          "tile_log2": m, "fusion": fusion, "compose": compose,
-          "avg_pass_GBps": round(nb / (pass_ms / max(cnt, 1) * 1e-3) / 1e9, 1),
-          "avg_pass_hbm_frac": round(nb / (pass_ms / max(cnt, 1) * 1e-3) / 1e9 / peaks()[0], 4),
-          "trace_error": abs(ok.orkan_trace(h) - 1.0)}
-    return h, st, exps
+    ok.orkan_init_state(h, ok.ORKAN_INIT_PURE, wl["psi"])
+    for q in range(n):
+        ok.orkan_depolarize(h, q, 0.1)
+    arr, keep, _ = circuit.marshal(wl["ops"], "schrodinger")
+    ok.orkan_run_circuit(h, arr, 0)
+    if sample is None:
+        rng = np.random.Generator(np.random.PCG64(20260415 + 21))
+        N = 1 << n
+        d = rng.integers(0, N, 4096)
+        rows = np.concatenate([rng.integers(0, N, 1 << 16), d])
+        cols = np.concatenate([rng.integers(0, N, 1 << 16), d])
+        sample = (rows, cols, d.size)
+    got = ok.orkan_get_elements(h, sample[0], sample[1])
+    ok.orkan_free(h)
+    del keep
+    return got, sample
+
+
+def brickwork_prefix(ok, circuit, torch, stream, n, dt, depth, hbm_peak):
+    """The first `depth` layers of the config-2 noisy brickwork (n = 16, Haar
+    1q on all qubits, Haar 2q on alternating pairs, depolarising 1e-3 on all)
+    in the given form, tile m = 5, fusion 8 with composition: ops/s and the
+    per-pass HBM fraction (2 x stored bytes / average pass time / hbm_gbs).
+    Every layer has the same op mix, so a prefix has the full circuit's
+    per-pass figures; `--workload brickwork` runs all 40 layers."""
+    from workloads import synth as S
+    rng = S.rng_for(S.BASE_SEED + 2)
+    psi = S.haar_state_vector(rng, 1 << n)
+    paulis = S.random_pauli_strings(rng, n, 32)
+    ops = S.brickwork(n, depth)
+    h, st, ex = _run_timed(ok, circuit, torch, stream, n, dt, 5, 8, True, ops, paulis, psi)
+    ok.orkan_free(h)
+    torch.cuda.empty_cache()
+    st.update({"n": n, "dtype": dt, "layers": depth, "ops": len(ops),
+               "state_bytes": ok.orkan_bytes(n, DTYPE_NAMES[dt], 5),
+               "pauli_expectations_abs_max": float(np.max(np.abs(ex))),
+               "workload": f"noisy brickwork n={n}, first {depth} of 40 layers (config 2), m=5, fusion 8 composed"})
+    return st
 
 
 def brickwork_study(ok, circuit, torch, stream, n, dt, depth):
@@ -778,7 +832,7 @@ def main(argv=None):
         mhz = clocks.get("sm_mhz") or 2070.0
         per = {k.replace("_per_s", "_per_sm_clk"): round(v / sms / (mhz * 1e6), 2) for k, v in rates.items() if k.endswith("_per_s")}
         print(json.dumps({"workload": "pipes", "sms": sms, "rates": rates, "per_sm_per_clock": per, "clocks": clocks,
-                          "derived_alu_peaks_T": ALU_PEAK_TOPS}), flush=True)
+                          "derived_alu_peaks_T": {k: alu_peak_tops(k, sms) for k in UNIT_RATE}}), flush=True)
         return 0
     if args.workload in ("brickwork", "precision", "paper", "relabel"):
         if args.workload == "relabel":
@@ -828,7 +882,7 @@ def main(argv=None):
         cap = st["served_capacity"]
         line = {"metric": METRIC, "value": round(cap["ops_per_s"], 2), "unit": UNIT, "n_gpus": world, "steps": 1,
                 "warmup": 0, "ms_per_step": round(cap["elapsed_s"] * 1e3, 1), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "c128/c64 requests (c128 served in df64)",
+                "scaling": "weak", "vs_baseline": None, "dtype": "c128/c64 requests, each at its own dtype",
                 "data": "synthetic",
                 "config": {"workload": "serving: 5000 seeded requests, n~U{4..14}, depth~U{10..200} from the "
                                        "mixed op mix, 50/50 picture and dtype"},
@@ -890,44 +944,56 @@ def main(argv=None):
     h2d = 2 * runner.bytes + op_bytes
     d2h = 8 * (1 + len(wl["paulis"]) + 2 + 1) + 8
 
-    # ---- roofline of the dominant kernel (the fused pass kernel)
+    # ---- roofline of the dominant kernel (the fused pass kernel), on the HBM basis: algorithmic bytes
+    # (2 x stored bytes per pass) / average pass duration / measured copy bandwidth.  The pipe that
+    # does the arithmetic (FP64 for c128) is reported beside it as its own field.
     hbm_peak, peak_kind = peaks()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     avg_pass_ms = pass_ms / max(pass_cnt, 1)
     achieved = 2.0 * runner.bytes / (avg_pass_ms * 1e-3) / 1e9
     alu_ops = runner.work[0]
     alu_tops = alu_ops / (pass_ms * 1e-3) / 1e12 if pass_ms > 0 else 0.0
-    alu_peak = ALU_PEAK_TOPS[args.dtype]
+    alu_peak = alu_peak_tops(args.dtype, sms)
     trec = traffic_record(args.dtype)
-    hbm = {"achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
-           "peak_kind": f"{peak_kind} hbm_gbs"}
-    alu = {"achieved": round(alu_tops, 2), "peak": round(alu_peak, 2),
-           "unit": "Tops/s (" + ("FP64-pipe ops" if args.dtype == "c128" else "FP32-pipe lane ops") + ")",
-           "frac": round(alu_tops / alu_peak, 4),
-           "peak_kind": "derived: 152 SMs x pipe rate per clock (measured probe) x 2.07 GHz",
-           "algorithmic_ops_per_launch": round(alu_ops / max(pass_cnt, 1))}
-    # the binding roofline is the one the pass kernel runs closer to
-    bound = "alu" if alu["frac"] >= hbm["frac"] else "hbm"
-    main = alu if bound == "alu" else hbm
-    roofline = {"bound": bound, "achieved": main["achieved"], "peak": main["peak"], "unit": main["unit"],
-                "frac": main["frac"], "traffic": (trec or {}).get("bytes_per_launch"),
-                "kernel": "pass_kernel (fused tile-group conjugation)", "peak_kind": main["peak_kind"],
-                "hbm": hbm, "alu": alu,
+    pipe_name = "fp64_pipe" if args.dtype == "c128" else "fp32_pipe"
+    pipe = {"achieved": round(alu_tops, 4), "peak": round(alu_peak, 4),
+            "unit": "Tops/s (" + ("FP64 operations" if args.dtype == "c128" else "FP32 lane operations") + ")",
+            "frac": round(alu_tops / alu_peak, 4),
+            "peak_kind": f"derived: {sms} SMs (device) x {UNIT_RATE[args.dtype]:g} per SM per clock x 2.07 GHz",
+            "algorithmic_ops_per_launch": round(alu_ops / max(pass_cnt, 1)),
+            "ops_counted": "the arithmetic each op form needs per stored element (no addressing or data movement)"}
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": (trec or {}).get("bytes_per_launch"),
+                "kernel": "pass_kernel (fused tile-group conjugation)", "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                pipe_name: pipe,
                 "algorithmic_bytes_per_launch": 2 * runner.bytes, "avg_launch_ms": round(avg_pass_ms, 4),
                 "launches": pass_cnt, "pass_share_of_step": round(pass_ms / ms, 4) if ms > 0 else None}
     runner.free()
 
-    # ---- comparison runs (rank 0 only): plain FP64 one-op-per-pass, fused c128, c64
+    # ---- comparison runs (rank 0 only): plain FP64 one-op-per-pass, and the declared faster forms (double-float
+    # and complex64), each with its error against the native FP64 run on one Schroedinger sweep
     variants = {}
     if not args.no_variants and world == 1:
+        ref_elems, samp = sweep_elements(ok, circuit, wl, n, m, "c128", args.fusion, compose, stream)
         for name, dt, fus, comp in (("c128_plain_unfused", "c128", 1, False), ("c128_fused", "c128", args.fusion, True),
-                                    ("df64_unfused", "df64", 1, False), ("c64_fused", "c64", args.fusion, True)):
+                                    ("df64_fused", "df64", args.fusion, True), ("df64_unfused", "df64", 1, False),
+                                    ("c64_fused", "c64", args.fusion, True)):
             if dt == args.dtype and fus == args.fusion and comp == compose:
                 continue
             r = Runner(ok, circuit, wl, n, m, dt, fus, comp, stream)
             vms, vpass, vcnt, _ = time_steps(r, max(2, args.steps // 3), 1, torch)
             variants[name] = {"value": round(r.ops_per_step * max(2, args.steps // 3) / (vms / 1e3), 1), "unit": UNIT,
+                              "dtype": dt, "fusion": fus,
                               "avg_pass_GBps": round(2.0 * r.bytes / (vpass / max(vcnt, 1) * 1e-3) / 1e9, 1)}
             r.free()
+            got, _ = sweep_elements(ok, circuit, wl, n, m, dt, fus, comp, stream, samp)
+            variants[name]["max_abs_err_vs_c128"] = float(np.max(np.abs(got - ref_elems)))
+            variants[name]["error_sample"] = (f"{samp[0].size} sampled elements (incl. {samp[2]} diagonal) after one "
+                                              f"Schroedinger sweep, against the native FP64 fused run")
+
+    bw16 = None
+    if not args.no_variants and world == 1 and args.bw_depth > 0:
+        bw16 = brickwork_prefix(ok, circuit, torch, stream, 16, "c128", args.bw_depth, hbm_peak)
 
     per_op = None
     serving_res = None
@@ -962,6 +1028,7 @@ def main(argv=None):
             "gpu_launches": launches,
             "clocks": clocks,
             "variants": variants,
+            "brickwork_n16": bw16,
             "per_op_pass_GBps": per_op,
             "serving": serving_res,
         }
