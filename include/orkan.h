@@ -183,6 +183,30 @@ int orkan_set_picture(orkan_h h, int picture);
 int orkan_load_tiled(orkan_h h, const void *host_src, int picture);
 int orkan_store_tiled(orkan_h h, void *host_dst);
 
+/* Checkpoints (not in the paper): a header of ORKAN_CKPT_HEADER_BYTES bytes
+ * followed by the raw tiled array (Sec. III-B layout) as the handle holds
+ * it, in physical qubit order, so saving needs no relabelling pass.  Header,
+ * little-endian: 8 bytes magic "ORKANCK1"; int32 version (1), n, tile_log2,
+ * dtype, picture, 0; int32 phys[64] (physical position of logical qubit q,
+ * q < n; entries from n on are q); uint64 data bytes (= orkan_bytes(n,
+ * dtype, tile_log2)); uint64 checksum of the data (FNV-1a over 64-bit
+ * little-endian words: h = 0xcbf29ce484222325, h = (h ^ w) * 0x100000001b3);
+ * zero padding to ORKAN_CKPT_HEADER_BYTES.  Host buffers are the caller's.
+ *   orkan_checkpoint_bytes: bytes a checkpoint of h takes (0 for NULL).
+ *   orkan_checkpoint_save: flush h's pending ops and write its checkpoint to
+ *     host_dst (cap bytes; EINVAL if smaller than orkan_checkpoint_bytes).
+ *   orkan_checkpoint_load: check the header (magic, version, sizes, labels,
+ *     checksum) and that n, tile_log2 and dtype equal h's, then load the data,
+ *     the picture and the labels into h.  A mismatch is EINVAL with both
+ *     shapes named, and leaves h unchanged.
+ *   orkan_checkpoint_inspect: host only (no GPU), the same checks and the
+ *     header's n, dtype, tile_log2 and picture (any output may be NULL). */
+#define ORKAN_CKPT_HEADER_BYTES 320
+size_t orkan_checkpoint_bytes(orkan_h h);
+int orkan_checkpoint_save(orkan_h h, void *host_dst, size_t cap);
+int orkan_checkpoint_load(orkan_h h, const void *host_src, size_t bytes);
+int orkan_checkpoint_inspect(const void *host_src, size_t bytes, int *n, int *dtype, int *tile_log2, int *picture);
+
 /* orkan_load_tiled without the wait: the copy is queued on the handle's
  * stream and the call returns.  Later calls on h are ordered after the copy;
  * host_src must stay valid and unchanged until it has completed (after

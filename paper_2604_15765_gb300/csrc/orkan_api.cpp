@@ -848,6 +848,55 @@ struct GraphRec {
   int phys_end[64];
 };
 
+// Checkpoint header (layout documented beside orkan_checkpoint_save).
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t version, n, tile_log2, dtype, picture, reserved;
+  int32_t phys[64];
+  uint64_t data_bytes;
+  uint64_t checksum;
+};
+static_assert(sizeof(CkptHeader) <= ORKAN_CKPT_HEADER_BYTES, "checkpoint header too large");
+constexpr char kCkptMagic[8] = {'O', 'R', 'K', 'A', 'N', 'C', 'K', '1'};
+
+// FNV-1a over 64-bit little-endian words (the data is a whole number of 8-byte words).
+uint64_t ckpt_checksum(const unsigned char* p, uint64_t bytes) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (uint64_t i = 0; i + 8 <= bytes; i += 8) {
+    uint64_t w = 0;
+    for (int b = 0; b < 8; ++b) w |= uint64_t(p[i + b]) << (8 * b);
+    h = (h ^ w) * 0x100000001b3ull;
+  }
+  return h;
+}
+
+int ckpt_parse(const void* src, size_t bytes, CkptHeader* hd) {
+  if (!src) return fail(ORKAN_EINVAL, "null checkpoint");
+  if (bytes < ORKAN_CKPT_HEADER_BYTES) return fail(ORKAN_EINVAL, "checkpoint shorter than its header");
+  std::memcpy(hd, src, sizeof(CkptHeader));
+  if (std::memcmp(hd->magic, kCkptMagic, 8) != 0) return fail(ORKAN_EINVAL, "not an Orkan checkpoint (bad magic)");
+  if (hd->version != 1) return fail(ORKAN_EINVAL, "unsupported checkpoint version");
+  Geometry g;
+  if (!valid_dtype(hd->dtype) || !geometry(hd->n, hd->tile_log2, &g))
+    return fail(ORKAN_EINVAL, "checkpoint header: bad n / dtype / tile_log2");
+  if (hd->picture != ORKAN_STATE && hd->picture != ORKAN_OBSERVABLE)
+    return fail(ORKAN_EINVAL, "checkpoint header: bad picture");
+  std::vector<char> seen(hd->n, 0);
+  for (int q = 0; q < hd->n; ++q) {
+    if (hd->phys[q] < 0 || hd->phys[q] >= hd->n || seen[hd->phys[q]])
+      return fail(ORKAN_EINVAL, "checkpoint header: labels are not a permutation");
+    seen[hd->phys[q]] = 1;
+  }
+  const uint64_t want = (uint64_t(g.ntiles) << (2 * g.m)) * elem_size(hd->dtype);
+  if (hd->data_bytes != want) return fail(ORKAN_EINVAL, "checkpoint header: data size does not match n / dtype / tile_log2");
+  if (bytes < ORKAN_CKPT_HEADER_BYTES + want) return fail(ORKAN_EINVAL, "checkpoint truncated");
+  const unsigned char* data = static_cast<const unsigned char*>(src) + ORKAN_CKPT_HEADER_BYTES;
+  if (ckpt_checksum(data, want) != hd->checksum) return fail(ORKAN_EINVAL, "checkpoint data checksum mismatch");
+  return ORKAN_OK;
+}
+}  // namespace
+
 // =================================================================== C ABI
 extern "C" {
 
@@ -1087,6 +1136,63 @@ int orkan_store_tiled(orkan_h h, void* host_dst) {
   if (int st = flush_pending(h)) return st;
   ORKAN_CUDA(cudaMemcpyAsync(host_dst, h->d_state, h->bytes, cudaMemcpyDeviceToHost, h->stream));
   ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+  return ORKAN_OK;
+}
+
+// ------------------------------------------------------------------ checkpoints
+
+size_t orkan_checkpoint_bytes(orkan_h h) { return h ? ORKAN_CKPT_HEADER_BYTES + h->bytes : 0; }
+
+int orkan_checkpoint_save(orkan_h h, void* host_dst, size_t cap) {
+  if (int st = check_blocking(h)) return st;
+  if (!host_dst) return fail(ORKAN_EINVAL, "null destination");
+  if (cap < ORKAN_CKPT_HEADER_BYTES + h->bytes) return fail(ORKAN_EINVAL, "destination smaller than orkan_checkpoint_bytes");
+  if (int st = flush_pending(h)) return st;
+  unsigned char* data = static_cast<unsigned char*>(host_dst) + ORKAN_CKPT_HEADER_BYTES;
+  ORKAN_CUDA(cudaMemcpyAsync(data, h->d_state, h->bytes, cudaMemcpyDeviceToHost, h->stream));
+  ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = 1;
+  hd.n = h->g.n;
+  hd.tile_log2 = h->g.m;
+  hd.dtype = h->dtype;
+  hd.picture = h->picture;
+  for (int q = 0; q < 64; ++q) hd.phys[q] = h->phys[q];
+  hd.data_bytes = h->bytes;
+  hd.checksum = ckpt_checksum(data, h->bytes);
+  std::memset(host_dst, 0, ORKAN_CKPT_HEADER_BYTES);
+  std::memcpy(host_dst, &hd, sizeof(hd));
+  return ORKAN_OK;
+}
+
+int orkan_checkpoint_load(orkan_h h, const void* host_src, size_t bytes) {
+  if (int st = check_blocking(h)) return st;
+  CkptHeader hd;
+  if (int st = ckpt_parse(host_src, bytes, &hd)) return st;
+  if (hd.n != h->g.n || hd.tile_log2 != h->g.m || hd.dtype != h->dtype)
+    return fail(ORKAN_EINVAL, "checkpoint is for n=" + std::to_string(hd.n) + " tile_log2=" +
+                                  std::to_string(hd.tile_log2) + " dtype=" + std::to_string(hd.dtype) +
+                                  ", the handle has n=" + std::to_string(h->g.n) + " tile_log2=" +
+                                  std::to_string(h->g.m) + " dtype=" + std::to_string(h->dtype));
+  h->pending.clear();
+  const unsigned char* data = static_cast<const unsigned char*>(host_src) + ORKAN_CKPT_HEADER_BYTES;
+  ORKAN_CUDA(cudaMemcpyAsync(h->d_state, data, h->bytes, cudaMemcpyHostToDevice, h->stream));
+  ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+  reset_labels(h);
+  for (int q = 0; q < h->g.n; ++q) h->phys[q] = hd.phys[q];
+  h->picture = hd.picture;
+  return ORKAN_OK;
+}
+
+int orkan_checkpoint_inspect(const void* host_src, size_t bytes, int* n, int* dtype, int* tile_log2, int* picture) {
+  CkptHeader hd;
+  if (int st = ckpt_parse(host_src, bytes, &hd)) return st;
+  if (n) *n = hd.n;
+  if (dtype) *dtype = hd.dtype;
+  if (tile_log2) *tile_log2 = hd.tile_log2;
+  if (picture) *picture = hd.picture;
   return ORKAN_OK;
 }
 

@@ -107,6 +107,10 @@ _SIGS = {
     "orkan_packed_depolarize": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p]),
     "orkan_packed_from_tiled": (C.c_int, [_h, C.c_void_p]),
     "orkan_packed_to_tiled": (C.c_int, [_h, C.c_void_p]),
+    "orkan_checkpoint_bytes": (C.c_size_t, [_h]),
+    "orkan_checkpoint_save": (C.c_int, [_h, C.c_void_p, C.c_size_t]),
+    "orkan_checkpoint_load": (C.c_int, [_h, C.c_void_p, C.c_size_t]),
+    "orkan_checkpoint_inspect": (C.c_int, [C.c_void_p, C.c_size_t, _pi, _pi, _pi, _pi]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -242,6 +246,30 @@ def orkan_load_tiled_async(h, host_buf: np.ndarray, picture: int = ORKAN_STATE):
 def orkan_store_tiled(h, host_buf: np.ndarray):
     assert host_buf.flags["C_CONTIGUOUS"]
     _check(_lib.orkan_store_tiled(h, host_buf.ctypes.data_as(C.c_void_p)), "orkan_store_tiled")
+
+
+ORKAN_CKPT_HEADER_BYTES = 320
+
+
+def orkan_checkpoint_save(h) -> np.ndarray:
+    """The handle's checkpoint (header + raw tiled array) as a uint8 array."""
+    buf = np.empty(int(_lib.orkan_checkpoint_bytes(h)), dtype=np.uint8)
+    _check(_lib.orkan_checkpoint_save(h, buf.ctypes.data_as(C.c_void_p), buf.size), "orkan_checkpoint_save")
+    return buf
+
+
+def orkan_checkpoint_load(h, buf):
+    buf = np.ascontiguousarray(np.frombuffer(buf, dtype=np.uint8) if not isinstance(buf, np.ndarray) else buf)
+    _check(_lib.orkan_checkpoint_load(h, buf.ctypes.data_as(C.c_void_p), buf.nbytes), "orkan_checkpoint_load")
+
+
+def orkan_checkpoint_inspect(buf) -> dict:
+    """Header fields of a checkpoint after its checks (host only)."""
+    buf = np.ascontiguousarray(np.frombuffer(buf, dtype=np.uint8) if not isinstance(buf, np.ndarray) else buf)
+    n, dt, m, pic = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _check(_lib.orkan_checkpoint_inspect(buf.ctypes.data_as(C.c_void_p), buf.nbytes, C.byref(n), C.byref(dt),
+                                         C.byref(m), C.byref(pic)), "orkan_checkpoint_inspect")
+    return {"n": n.value, "dtype": dt.value, "tile_log2": m.value, "picture": pic.value}
 
 
 # ------------------------------------------------------------------ ops
