@@ -427,6 +427,42 @@ def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=
     return out
 
 
+def _run_timed(ok, circuit, torch, stream, n, dt, m, fusion, compose, ops, paulis, psi):
+    """One operator through ops, then the Pauli strings; device time, pass stats, handle."""
+    h = ok.orkan_alloc(n, DTYPE_NAMES[dt], m)
+    ok.orkan_set_stream(h, stream)
+    ok.orkan_set_fusion(h, fusion, compose)
+    ok.orkan_init_state(h, ok.ORKAN_INIT_PURE, psi)
+    ok.orkan_sync(h)
+    ok.orkan_set_timing(h, True)
+    ok.orkan_pass_time(h)
+    ok.orkan_pass_work(h)
+    p0 = ok.orkan_stats(h)["passes"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for op in ops:
+        circuit.apply_op(h, op)
+    ok.orkan_flush(h)
+    ev1.record()
+    exps = np.array([ok.orkan_expect_pauli(h, s) for s in paulis])
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    pass_ms, cnt = ok.orkan_pass_time(h)
+    work, _ = ok.orkan_pass_work(h)
+    ok.orkan_set_timing(h, False)
+    nb = 2 * ok.orkan_bytes(n, DTYPE_NAMES[dt], m)
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    st = {"ops_per_s": round(len(ops) / (ms / 1e3), 1), "ms": round(ms, 1), "passes": ok.orkan_stats(h)["passes"] - p0,
+          "tile_log2": m, "fusion": fusion, "compose": compose,
+          "avg_pass_GBps": round(nb / (pass_ms / max(cnt, 1) * 1e-3) / 1e9, 1),
+          "avg_pass_hbm_frac": round(nb / (pass_ms / max(cnt, 1) * 1e-3) / 1e9 / peaks()[0], 4),
+          "pass_share": round(pass_ms / ms, 4) if ms > 0 else None,
+          ("fp64_pipe_frac" if dt == "c128" else "fp32_pipe_frac"):
+              round(work / (pass_ms * 1e-3) / 1e12 / alu_peak_tops(dt, sms), 4) if pass_ms > 0 else None,
+          "trace_error": abs(ok.orkan_trace(h) - 1.0)}
+    return h, st, exps
+
+
 def sweep_elements(ok, circuit, wl, n, m, dt, fusion, compose, stream, sample=None):
     """One Schroedinger sweep from the bench's initial state (the Haar pure
     state depolarised on every qubit) in the given form; returns sampled
