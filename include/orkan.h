@@ -54,6 +54,7 @@ extern "C" {
 #define ORKAN_EZEROPROB (-4) /* measurement: the selected outcome has probability < 1e-300 */
 #define ORKAN_EPICTURE (-5)  /* operation not defined in the handle's picture */
 #define ORKAN_ENODEV (-6)    /* no CUDA device */
+#define ORKAN_ETIMEOUT (-7)  /* a bounded device-side wait ran out (orkan_run_batch gang barrier) */
 
 /* Storage dtype.
  *   ORKAN_C128: complex128 elements, native FP64 arithmetic (16 B/element).
@@ -284,6 +285,77 @@ typedef struct {
  * the number of ops applied.  One call per circuit keeps host overhead per op
  * in the microseconds. */
 int orkan_run_circuit(orkan_h h, int count, const orkan_op *ops, int *outcomes, double *probs, int *done);
+
+/* ------------------------------------------------------------------ batched circuits
+ * Many small operators' whole circuits in one persistent launch per dtype:
+ * Eq. (1) / Eq. (2) block updates of Algorithm 1 on each tiled array
+ * (Sec. III-B), Z projections with Born renormalisation (Sec. II trace
+ * non-increasing maps, renormalised as orkan_measure does), then the
+ * readouts tr(P H) (Pauli strings) and <psi|H|psi> (Sec. III-C mean value
+ * against a pure state).  For operators whose per-op passes are too short
+ * to fill the GPU (n up to ~10): CTAs take work slots from a device queue;
+ * an operator that fits shared memory (n <= 7) runs its whole circuit in one
+ * CTA with one read and one write of its array, a larger one on a gang of
+ * CTAs that meet at a time-limited barrier between ops.  Results depend only
+ * on the item itself (fixed reduction orders), never on the rest of the
+ * batch.
+ *
+ * Per item:
+ *   h       the operator's handle (its n, dtype, tile size and memory); its
+ *           pending ops are flushed and its stream waited for first.
+ *   init    ORKAN_BATCH_KEEP: h's current operator, picture and labels;
+ *           ORKAN_INIT_PURE: rho = psi psi^dagger from init_data (N complex,
+ *           2 N doubles), picture STATE, labels reset;
+ *           ORKAN_BATCH_PAULI_SUM: O = sum_t coeffs[t] P_t from nterms strings
+ *           `terms` (nterms * n characters of IXYZ, character l on qubit l),
+ *           picture OBSERVABLE, labels reset.
+ *   nops, ops  the circuit, with orkan_run_circuit's op semantics (MEASURE
+ *           only on states; on an observable every op applies Phi*).
+ *           k = 1 maps run as their Pauli transfer matrix, k = 2, 3 as Kraus
+ *           sweeps (at most 16 operators).  No fusion or composition.
+ *   npaulis, paulis  readout strings (npaulis * n characters), logical qubits.
+ *   psi     readout vector (N complex, logical index order) or NULL.
+ *   out     host: npaulis values tr(P H), then <psi|H|psi> if psi.
+ *   outcomes, probs  host, one per MEASURE op (either may be NULL).
+ *   gang    0: automatic (1 when the array fits shared memory, else about
+ *           one CTA per 32 Ki stored elements, at most 64); else the number
+ *           of CTAs to use (1..64).
+ *   status  written by the call: ORKAN_OK, ORKAN_EZEROPROB (a measurement
+ *           outcome had probability <= 1e-300; the item stopped there) or
+ *           ORKAN_ETIMEOUT (its gang did not assemble within the wait limit,
+ *           e.g. a gang larger than the grid; the item stopped there).
+ * The call validates every item before launching (EINVAL / EPICTURE name
+ * the item), blocks until the results are on the host and returns ORKAN_OK
+ * when every item succeeded, else the first failing item's status.  Work
+ * runs on cuda_stream (NULL = the legacy default stream).  Handles must be
+ * distinct and on the current device.  Calls from several host threads are
+ * serialised per device (a gang needs every CTA of its launch resident). */
+#define ORKAN_BATCH_KEEP (-1)
+#define ORKAN_BATCH_PAULI_SUM 4
+typedef struct {
+  orkan_h h;
+  int init;
+  const double *init_data;
+  int nterms;
+  const char *terms;
+  const double *coeffs;
+  int nops;
+  const orkan_op *ops;
+  int npaulis;
+  const char *paulis;
+  const double *psi;
+  double *out;
+  int *outcomes;
+  double *probs;
+  int gang;
+  int status;
+} orkan_batch_item;
+int orkan_run_batch(int count, orkan_batch_item *items, void *cuda_stream);
+
+/* Process-wide limits of orkan_run_batch: at most max_ctas CTAs per launch
+ * (0 = as many as can be resident, which is also the upper bound), and the
+ * time limit of one gang barrier in seconds (default 1.0; 1e-6 .. 60). */
+int orkan_batch_limits(int max_ctas, double wait_seconds);
 
 /* ------------------------------------------------------------------ readouts (block; FP64) */
 

@@ -89,3 +89,67 @@ def run_circuit(h, ops, picture: str = "schrodinger", native: bool = True):
     if picture == "schrodinger":
         return list(zip(outs, probs))
     return [(0 if op["u"] < 0.5 else 1, None) for op in ops if op["kind"] == "measure"]
+
+
+def run_batch(requests, stream_ptr=None):
+    """Marshal requests into one orkan_run_batch call.  Each request is a dict:
+      h        handle; init: "pure" (psi0), "pauli_sum" (terms, coeffs) or "keep";
+      ops      op dicts (measurements become projections on observables);
+      paulis   readout strings (optional); psi: readout vector (optional);
+      gang     CTAs (0 / absent = automatic).
+    Returns one dict per request: out (tr(P H) per string, then <psi|H|psi>),
+    outcomes, probs, status."""
+    import numpy as np
+    keep = []
+    items = []
+    outs = []
+    for r in requests:
+        it = ok.OrkanBatchItem()
+        it.h = r["h"]
+        init = r.get("init", "keep")
+        picture = "heisenberg" if init == "pauli_sum" else "schrodinger"
+        if init == "keep":
+            it.init = ok.ORKAN_BATCH_KEEP
+            picture = r.get("picture", "schrodinger")
+        elif init == "pure":
+            it.init = ok.ORKAN_INIT_PURE
+            psi0 = np.ascontiguousarray(np.asarray(r["psi0"], np.complex128))
+            keep.append(psi0)
+            it.init_data = psi0.view(np.float64).ctypes.data_as(ok._pd)
+        else:
+            it.init = ok.ORKAN_BATCH_PAULI_SUM
+            terms = "".join(r["terms"]).encode()
+            cs = np.ascontiguousarray(np.asarray(r["coeffs"], np.float64))
+            keep += [terms, cs]
+            it.nterms = len(r["terms"])
+            it.terms = terms
+            it.coeffs = cs.ctypes.data_as(ok._pd)
+        arr, kk, nmeas = marshal(r.get("ops", []), picture)
+        keep += [arr, kk]
+        it.nops = len(r.get("ops", []))
+        it.ops = arr
+        paulis = r.get("paulis", [])
+        it.npaulis = len(paulis)
+        if paulis:
+            ps = "".join(paulis).encode()
+            keep.append(ps)
+            it.paulis = ps
+        psi = r.get("psi")
+        nout = len(paulis) + (0 if psi is None else 1)
+        out = np.zeros(max(nout, 1))
+        if psi is not None:
+            pv = np.ascontiguousarray(np.asarray(psi, np.complex128))
+            keep.append(pv)
+            it.psi = pv.view(np.float64).ctypes.data_as(ok._pd)
+        it.out = out.ctypes.data_as(ok._pd)
+        oc = np.zeros(max(nmeas, 1), dtype=np.int32)
+        pr = np.zeros(max(nmeas, 1))
+        it.outcomes = oc.ctypes.data_as(ok._pi)
+        it.probs = pr.ctypes.data_as(ok._pd)
+        it.gang = int(r.get("gang", 0))
+        outs.append((out, nout, oc, pr, nmeas))
+        items.append(it)
+    statuses = ok.orkan_run_batch(items, stream_ptr)
+    del keep
+    return [{"out": out[:nout].copy(), "outcomes": [int(x) for x in oc[:nm]], "probs": [float(x) for x in pr[:nm]],
+             "status": s} for (out, nout, oc, pr, nm), s in zip(outs, statuses)]

@@ -909,6 +909,7 @@ const char* orkan_strerror(int status) {
     case ORKAN_EZEROPROB: return "zero-probability outcome";
     case ORKAN_EPICTURE: return "operation not defined in this picture";
     case ORKAN_ENODEV: return "no CUDA device";
+    case ORKAN_ETIMEOUT: return "a bounded device wait ran out";
   }
   return "unknown status";
 }
@@ -1847,5 +1848,458 @@ extern "C" int orkan_autotune(int n, int dtype, int* tile_log2, int* max_ops) {
   }
   *tile_log2 = best_m;
   *max_ops = best_f;
+  return ORKAN_OK;
+}
+
+// =================================================================== batched circuits
+// Host side of orkan_run_batch: every item's ops are prepared in FP64 (Pauli
+// transfer matrices for k = 1, qubit-ordered Kraus matrices for k = 2, 3,
+// adjoints on observables), packed with the item table, the work slots and
+// the readout data into one upload, and run by one persistent launch per
+// dtype (batch_kernels.cu).
+namespace {
+
+std::mutex g_batch_mutex;          // one batch launch at a time (gangs need their grid resident)
+int g_batch_max_ctas = 0;
+double g_batch_wait_s = 1.0;
+
+struct BatchArena {
+  void* dev = nullptr;
+  size_t dev_cap = 0;
+  unsigned char* host = nullptr;   // pinned
+  size_t host_cap = 0;
+};
+std::map<int, BatchArena> g_batch_arenas;
+
+int arena_reserve(BatchArena& a, size_t bytes) {
+  if (bytes > a.dev_cap) {
+    if (a.dev) cudaFree(a.dev);
+    a.dev = nullptr;
+    a.dev_cap = 0;
+    if (cudaMalloc(&a.dev, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ORKAN_ENOMEM, "batch: device buffer allocation failed");
+    }
+    a.dev_cap = bytes;
+  }
+  if (bytes > a.host_cap) {
+    if (a.host) cudaFreeHost(a.host);
+    a.host = nullptr;
+    a.host_cap = 0;
+    if (cudaMallocHost(reinterpret_cast<void**>(&a.host), bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ORKAN_ENOMEM, "batch: pinned host buffer allocation failed");
+    }
+    a.host_cap = bytes;
+  }
+  return ORKAN_OK;
+}
+
+// Bytes of shared memory a gang-1 item may use for its array.
+constexpr size_t kBatchSmemCap = 160 * 1024;
+
+struct PackedBatch {
+  std::vector<BatchItem> items;
+  std::vector<BatchOp> ops;
+  std::vector<double> coef;
+  std::vector<unsigned char> aux;
+  std::vector<int32_t> slot_item;
+  std::vector<int> src;            // item -> index in the caller's array
+  std::vector<std::vector<int>> ny;   // per item: Y count of each readout string
+  int nres = 0, nmeas = 0;
+  int64_t npart = 0;
+  size_t smem = 0;
+};
+
+size_t aux_put(std::vector<unsigned char>& aux, const void* p, size_t bytes) {
+  size_t off = (aux.size() + 15) & ~size_t(15);
+  aux.resize(off + bytes);
+  std::memcpy(aux.data() + off, p, bytes);
+  return off;
+}
+
+int batch_fail(int item, int code, const std::string& msg) {
+  return fail(code, "batch item " + std::to_string(item) + ": " + msg);
+}
+
+// Kraus set of one op in the caller's qubit order (k = 1 channels built here).
+int batch_kraus(const orkan_op& o, int item, std::vector<Mat>* out) {
+  const int d = 1 << o.k;
+  out->clear();
+  auto m2 = [](cd a, cd b, cd c, cd dd) { return Mat{a, b, c, dd}; };
+  switch (o.kind) {
+    case ORKAN_OP_UNITARY:
+      if (!o.mats) return batch_fail(item, ORKAN_EINVAL, "null matrix");
+      out->push_back(read_mat(o.mats, d));
+      return ORKAN_OK;
+    case ORKAN_OP_KRAUS:
+      if (!o.mats || o.r < 1 || o.r > (1 << (2 * o.k)) || (o.k > 1 && o.r > kK3MaxTerms))
+        return batch_fail(item, ORKAN_EINVAL, "need 1 <= r <= min(4^k, 16) Kraus operators");
+      for (int t = 0; t < o.r; ++t) out->push_back(read_mat(o.mats + size_t(2) * d * d * t, d));
+      return ORKAN_OK;
+    case ORKAN_OP_DEPOLARIZE: {
+      const double p = o.param;
+      if (!(p >= 0.0 && p <= 1.0)) return batch_fail(item, ORKAN_EINVAL, "p must be in [0, 1]");
+      const double a = std::sqrt(1.0 - p), b = std::sqrt(p / 3.0);
+      *out = {m2(a, 0, 0, a), m2(0, b, b, 0), m2(0, cd(0, -b), cd(0, b), 0), m2(b, 0, 0, -b)};
+      return ORKAN_OK;
+    }
+    case ORKAN_OP_DEPHASE: {
+      const double p = o.param;
+      if (!(p >= 0.0 && p <= 1.0)) return batch_fail(item, ORKAN_EINVAL, "p must be in [0, 1]");
+      const double a = std::sqrt(1.0 - p), b = std::sqrt(p);
+      *out = {m2(a, 0, 0, a), m2(b, 0, 0, -b)};
+      return ORKAN_OK;
+    }
+    case ORKAN_OP_AMPDAMP: {
+      const double g = o.param;
+      if (!(g >= 0.0 && g <= 1.0)) return batch_fail(item, ORKAN_EINVAL, "gamma must be in [0, 1]");
+      *out = {m2(1, 0, 0, std::sqrt(1.0 - g)), m2(0, std::sqrt(g), 0, 0)};
+      return ORKAN_OK;
+    }
+  }
+  return batch_fail(item, ORKAN_EINVAL, "unknown op kind");
+}
+
+// Pauli string (n characters, logical) -> physical masks (x, z, y) and Y count.
+int batch_pauli(const char* s, int n, const int* phys, uint64_t m[3], int* ny, int item) {
+  m[0] = m[1] = m[2] = 0;
+  *ny = 0;
+  for (int l = 0; l < n; ++l) {
+    const uint64_t bit = uint64_t(1) << phys[l];
+    switch (s[l]) {
+      case 'I': break;
+      case 'X': m[0] |= bit; break;
+      case 'Y': m[0] |= bit; m[2] |= bit; ++*ny; break;
+      case 'Z': m[1] |= bit; break;
+      default: return batch_fail(item, ORKAN_EINVAL, "Pauli characters must be I, X, Y or Z");
+    }
+  }
+  return ORKAN_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Validate item `idx` and append it to the dtype group's tables.
+int batch_pack_item(const orkan_batch_item& it, int idx, PackedBatch* pb) {
+  orkan_ctx* h = it.h;
+  const int n = h->g.n, m = h->g.m, dtype = h->dtype;
+  const int64_t N = int64_t(1) << n;
+  int phys[64];
+  for (int q = 0; q < 64; ++q) phys[q] = q;
+  int picture = h->picture;
+  if (it.init == ORKAN_BATCH_KEEP) {
+    std::copy(h->phys, h->phys + 64, phys);
+  } else if (it.init == ORKAN_INIT_PURE) {
+    if (!it.init_data) return batch_fail(idx, ORKAN_EINVAL, "ORKAN_INIT_PURE needs init_data");
+    picture = ORKAN_STATE;
+  } else if (it.init == ORKAN_BATCH_PAULI_SUM) {
+    if (it.nterms < 0 || (it.nterms > 0 && (!it.terms || !it.coeffs)))
+      return batch_fail(idx, ORKAN_EINVAL, "bad Pauli-sum terms");
+    picture = ORKAN_OBSERVABLE;
+  } else {
+    return batch_fail(idx, ORKAN_EINVAL, "init must be ORKAN_BATCH_KEEP, ORKAN_INIT_PURE or ORKAN_BATCH_PAULI_SUM");
+  }
+  const bool adj = picture == ORKAN_OBSERVABLE;
+  if (it.nops < 0 || (it.nops > 0 && !it.ops)) return batch_fail(idx, ORKAN_EINVAL, "bad op list");
+  if (it.npaulis < 0 || (it.npaulis > 0 && (!it.paulis || !it.out)) || (it.psi && !it.out))
+    return batch_fail(idx, ORKAN_EINVAL, "readouts need an output array");
+  if (it.gang < 0 || it.gang > 64) return batch_fail(idx, ORKAN_EINVAL, "gang must be 0 (automatic) or 1..64");
+
+  BatchItem I{};
+  I.state = reinterpret_cast<uint64_t>(h->d_state);
+  I.stored = int64_t(h->g.ntiles) << (2 * m);
+  I.n = n;
+  I.m = m;
+  I.psi_off = -1;
+  I.op_begin = int32_t(pb->ops.size());
+  int nmeas = 0;
+  for (int k = 0; k < it.nops; ++k) {
+    const orkan_op& o = it.ops[k];
+    BatchOp op{};
+    if (o.kind == ORKAN_OP_MEASURE || o.kind == ORKAN_OP_PROJECT) {
+      if (o.k != 1 && o.k != 0) return batch_fail(idx, ORKAN_EINVAL, "measure / project act on one qubit");
+      if (int st = check_qubits_n(n, 1, o.qubits)) return batch_fail(idx, st, g_last_error);
+      op.q[0] = phys[o.qubits[0]];
+      if (o.kind == ORKAN_OP_MEASURE) {
+        if (adj) return batch_fail(idx, ORKAN_EPICTURE, "measurement on an observable (use a projection)");
+        if (!(o.param >= 0.0 && o.param < 1.0)) return batch_fail(idx, ORKAN_EINVAL, "u must be in [0, 1)");
+        op.form = BF_MEASURE;
+        op.u = o.param;
+        op.meas = nmeas++;
+      } else {
+        if (o.outcome != 0 && o.outcome != 1) return batch_fail(idx, ORKAN_EINVAL, "outcome must be 0 or 1");
+        op.form = BF_PROJECT;
+        op.outcome = o.outcome;
+      }
+      pb->ops.push_back(op);
+      continue;
+    }
+    const int kq = (o.kind == ORKAN_OP_UNITARY || o.kind == ORKAN_OP_KRAUS) ? o.k : 1;
+    if (kq < 1 || kq > 3 || kq > n) return batch_fail(idx, ORKAN_EINVAL, "k must be 1, 2 or 3 and at most n");
+    if (int st = check_qubits_n(n, kq, o.qubits)) return batch_fail(idx, st, g_last_error);
+    orkan_op oo = o;
+    oo.k = kq;
+    std::vector<Mat> kraus;
+    if (int st = batch_kraus(oo, idx, &kraus)) return st;
+    int pq[3];
+    for (int l = 0; l < kq; ++l) pq[l] = phys[o.qubits[l]];
+    op.coef = int32_t(pb->coef.size());
+    if (kq == 1) {
+      op.form = BF_PTM1;
+      op.q[0] = pq[0];
+      const std::vector<double> R = ptm(1, kraus, adj);
+      for (int i = 0; i < 16; ++i) {
+        double slot;
+        pack_slot(dtype, &slot, 0.5 * R[i]);
+        pb->coef.push_back(slot);
+      }
+    } else {
+      // bit l of the caller's index is qubit pq[l]; re-index to ascending positions
+      int order[3] = {0, 1, 2};
+      std::sort(order, order + kq, [&](int x, int y) { return pq[x] < pq[y]; });
+      int rank[3] = {0, 0, 0};
+      for (int l = 0; l < kq; ++l) {
+        op.q[l] = pq[order[l]];
+        rank[order[l]] = l;
+      }
+      const int d = 1 << kq;
+      auto perm = [&](int x) {
+        int y = 0;
+        for (int l = 0; l < kq; ++l) y |= ((x >> l) & 1) << rank[l];
+        return y;
+      };
+      op.form = kq == 2 ? BF_KRAUS2 : BF_KRAUS3;
+      op.r = int32_t(kraus.size());
+      for (const Mat& K : kraus) {
+        Mat B(d * d);
+        for (int i = 0; i < d; ++i)
+          for (int j = 0; j < d; ++j) B[perm(i) * d + perm(j)] = K[i * d + j];
+        if (adj) B = dagger(B, d);   // Phi* applies L^dagger (.) L = M (.) M^dagger with M = L^dagger
+        for (int i = 0; i < d * d; ++i) {
+          double s0, s1;
+          pack_slot(dtype, &s0, B[i].real());
+          pack_slot(dtype, &s1, B[i].imag());
+          pb->coef.push_back(s0);
+          pb->coef.push_back(s1);
+        }
+      }
+    }
+    pb->ops.push_back(op);
+  }
+  I.op_end = int32_t(pb->ops.size());
+  I.meas_base = pb->nmeas;
+  pb->nmeas += nmeas;
+  // initial operator
+  if (it.init == ORKAN_INIT_PURE) {
+    I.init = 1;
+    I.init_off = int64_t(aux_put(pb->aux, it.init_data, size_t(16) * N));
+  } else if (it.init == ORKAN_BATCH_PAULI_SUM) {
+    I.init = 2;
+    I.nterms = it.nterms;
+    std::vector<uint64_t> tab(size_t(4) * it.nterms);
+    std::vector<double> cs(it.nterms);
+    for (int t = 0; t < it.nterms; ++t) {
+      uint64_t mk[3];
+      int ny = 0;
+      if (int st = batch_pauli(it.terms + size_t(t) * n, n, phys, mk, &ny, idx)) return st;
+      tab[4 * t] = mk[0];
+      tab[4 * t + 1] = mk[1];
+      tab[4 * t + 2] = mk[2];
+      tab[4 * t + 3] = uint64_t(ny);
+      cs[t] = it.coeffs[t];
+    }
+    std::vector<unsigned char> blob(tab.size() * 8 + cs.size() * 8);
+    if (!tab.empty()) std::memcpy(blob.data(), tab.data(), tab.size() * 8);
+    if (!cs.empty()) std::memcpy(blob.data() + tab.size() * 8, cs.data(), cs.size() * 8);
+    I.init_off = int64_t(aux_put(pb->aux, blob.data(), blob.size()));
+  }
+  // readouts
+  std::vector<int> nys(it.npaulis);
+  {
+    std::vector<uint64_t> tab(size_t(3) * it.npaulis);
+    for (int p = 0; p < it.npaulis; ++p)
+      if (int st = batch_pauli(it.paulis + size_t(p) * n, n, phys, &tab[3 * p], &nys[p], idx)) return st;
+    I.npauli = it.npaulis;
+    I.pauli_off = tab.empty() ? 0 : int64_t(aux_put(pb->aux, tab.data(), tab.size() * 8));
+  }
+  if (it.psi) {
+    std::vector<double> v(size_t(2) * N);
+    for (int64_t l = 0; l < N; ++l) {   // logical index l lives at physical index p
+      uint64_t p = 0;
+      for (int q = 0; q < n; ++q) p |= ((uint64_t(l) >> q) & 1u) << phys[q];
+      v[2 * p] = it.psi[2 * l];
+      v[2 * p + 1] = it.psi[2 * l + 1];
+    }
+    I.psi_off = int64_t(aux_put(pb->aux, v.data(), v.size() * 8));
+  }
+  I.res = pb->nres;
+  pb->nres += 2 * it.npaulis + (it.psi ? 1 : 0);
+  // gang and placement
+  const size_t bytes = h->bytes;
+  int G = it.gang;
+  if (G == 0) G = bytes <= kBatchSmemCap ? 1 : int(std::min<int64_t>(64, std::max<int64_t>(2, (I.stored + 32767) / 32768)));
+  I.gang = G;
+  I.smem = (G == 1 && bytes <= kBatchSmemCap) ? 1 : 0;
+  if (I.smem) pb->smem = std::max(pb->smem, (bytes + 15) & ~size_t(15));
+  I.part_stride = std::max(2, 2 * it.npaulis + 1);
+  I.part_off = pb->npart;
+  pb->npart += int64_t(G) * I.part_stride;
+  I.first_slot = int32_t(pb->slot_item.size());
+  for (int g = 0; g < G; ++g) pb->slot_item.push_back(int32_t(pb->items.size()));
+  pb->items.push_back(I);
+  pb->src.push_back(idx);
+  pb->ny.push_back(nys);
+  return ORKAN_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Upload, launch and read back one dtype group; statuses land in items[].status.
+int batch_run_group(int dtype, PackedBatch& pb, orkan_batch_item* items, cudaStream_t stream) {
+  if (pb.items.empty()) return ORKAN_OK;
+  int dev = 0, sms = 0;
+  ORKAN_CUDA(cudaGetDevice(&dev));
+  ORKAN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int nit = int(pb.items.size());
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  // upload region, then the zeroed region, then the outputs
+  size_t off = 0;
+  const size_t o_items = off; off = al(off + sizeof(BatchItem) * nit);
+  const size_t o_ops = off;   off = al(off + sizeof(BatchOp) * pb.ops.size());
+  const size_t o_coef = off;  off = al(off + 8 * pb.coef.size());
+  const size_t o_aux = off;   off = al(off + pb.aux.size());
+  const size_t o_slot = off;  off = al(off + 4 * pb.slot_item.size());
+  const size_t up_bytes = off;
+  const size_t o_cnt = off;   off = al(off + 4);
+  const size_t o_bar = off;   off = al(off + 4 * size_t(nit));
+  const size_t o_stat = off;  off = al(off + 4 * size_t(nit));
+  const size_t o_out = off;   off = al(off + 4 * size_t(pb.nmeas));
+  const size_t o_prob = off;  off = al(off + 8 * size_t(pb.nmeas));
+  const size_t o_res = off;   off = al(off + 8 * size_t(pb.nres));
+  const size_t zero_end = off;
+  const size_t o_part = off;  off = al(off + 8 * size_t(pb.npart));
+  const size_t total = off;
+  BatchArena& a = g_batch_arenas[dev];
+  if (int st = arena_reserve(a, total)) return st;
+  unsigned char* hb = a.host;
+  unsigned char* db = static_cast<unsigned char*>(a.dev);
+  std::memcpy(hb + o_items, pb.items.data(), sizeof(BatchItem) * nit);
+  if (!pb.ops.empty()) std::memcpy(hb + o_ops, pb.ops.data(), sizeof(BatchOp) * pb.ops.size());
+  if (!pb.coef.empty()) std::memcpy(hb + o_coef, pb.coef.data(), 8 * pb.coef.size());
+  if (!pb.aux.empty()) std::memcpy(hb + o_aux, pb.aux.data(), pb.aux.size());
+  std::memcpy(hb + o_slot, pb.slot_item.data(), 4 * pb.slot_item.size());
+  BatchDesc d{};
+  d.items = reinterpret_cast<const BatchItem*>(db + o_items);
+  d.ops = reinterpret_cast<const BatchOp*>(db + o_ops);
+  d.coef = reinterpret_cast<const double*>(db + o_coef);
+  d.aux = db + o_aux;
+  d.slot_item = reinterpret_cast<const int32_t*>(db + o_slot);
+  d.counter = reinterpret_cast<int32_t*>(db + o_cnt);
+  d.bar = reinterpret_cast<int32_t*>(db + o_bar);
+  d.status = reinterpret_cast<int32_t*>(db + o_stat);
+  d.outcomes = reinterpret_cast<int32_t*>(db + o_out);
+  d.probs = reinterpret_cast<double*>(db + o_prob);
+  d.results = reinterpret_cast<double*>(db + o_res);
+  d.partials = reinterpret_cast<double*>(db + o_part);
+  d.wait_ns = uint64_t(g_batch_wait_s * 1e9);
+  d.nslots = int32_t(pb.slot_item.size());
+  int per_sm = 0;
+  ORKAN_CUDA(batch_occupancy(dtype, pb.smem, &per_sm));
+  if (per_sm < 1) return fail(ORKAN_ECUDA, "batch: the kernel does not fit on an SM with this shared memory");
+  int grid = std::min<int64_t>(int64_t(per_sm) * sms, d.nslots);
+  if (g_batch_max_ctas > 0) grid = std::min(grid, g_batch_max_ctas);
+  ORKAN_CUDA(cudaMemcpyAsync(db, hb, up_bytes, cudaMemcpyHostToDevice, stream));
+  ORKAN_CUDA(cudaMemsetAsync(db + o_cnt, 0, zero_end - o_cnt, stream));
+  ORKAN_CUDA(launch_batch(dtype, d, grid, pb.smem, stream));
+  ORKAN_CUDA(cudaMemcpyAsync(hb + o_stat, db + o_stat, zero_end - o_stat, cudaMemcpyDeviceToHost, stream));
+  ORKAN_CUDA(cudaStreamSynchronize(stream));
+  const int32_t* st = reinterpret_cast<const int32_t*>(hb + o_stat);
+  const int32_t* outc = reinterpret_cast<const int32_t*>(hb + o_out);
+  const double* prob = reinterpret_cast<const double*>(hb + o_prob);
+  const double* res = reinterpret_cast<const double*>(hb + o_res);
+  for (int i = 0; i < nit; ++i) {
+    const BatchItem& I = pb.items[i];
+    orkan_batch_item& it = items[pb.src[i]];
+    it.status = st[i];
+    int nm = 0;
+    for (int k = I.op_begin; k < I.op_end; ++k)
+      if (pb.ops[k].form == BF_MEASURE) {
+        if (it.outcomes) it.outcomes[nm] = outc[I.meas_base + nm];
+        if (it.probs) it.probs[nm] = prob[I.meas_base + nm];
+        ++nm;
+      }
+    for (int p = 0; p < I.npauli; ++p) {
+      const double sr = res[I.res + 2 * p], si = res[I.res + 2 * p + 1];
+      switch (pb.ny[i][p] & 3) {   // tr(P H) = i^{nY} S
+        case 0: it.out[p] = sr; break;
+        case 1: it.out[p] = -si; break;
+        case 2: it.out[p] = -sr; break;
+        default: it.out[p] = si; break;
+      }
+    }
+    if (I.psi_off >= 0) it.out[I.npauli] = res[I.res + 2 * I.npauli];
+  }
+  return ORKAN_OK;
+}
+
+}  // namespace
+
+extern "C" int orkan_batch_limits(int max_ctas, double wait_seconds) {
+  if (max_ctas < 0 || !(wait_seconds >= 1e-6 && wait_seconds <= 60.0))
+    return fail(ORKAN_EINVAL, "max_ctas must be >= 0 and wait_seconds in [1e-6, 60]");
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  g_batch_max_ctas = max_ctas;
+  g_batch_wait_s = wait_seconds;
+  return ORKAN_OK;
+}
+
+extern "C" int orkan_run_batch(int count, orkan_batch_item* items, void* cuda_stream) {
+  if (count < 0 || (count > 0 && !items)) return fail(ORKAN_EINVAL, "bad item list");
+  if (count == 0) return ORKAN_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(ORKAN_ENODEV, "no CUDA device");
+  for (int i = 0; i < count; ++i) {
+    orkan_ctx* h = items[i].h;
+    if (int st = check_blocking(h)) return batch_fail(i, st, g_last_error);
+    if (h->device != dev) return batch_fail(i, ORKAN_EINVAL, "handle is on another device");
+    for (int j = 0; j < i; ++j)
+      if (items[j].h == h) return batch_fail(i, ORKAN_EINVAL, "handles must be distinct");
+  }
+  PackedBatch pb[3];
+  for (int i = 0; i < count; ++i) {
+    items[i].status = ORKAN_OK;
+    if (int st = batch_pack_item(items[i], i, &pb[items[i].h->dtype])) return st;
+  }
+  // the handles' own work comes first
+  for (int i = 0; i < count; ++i) {
+    orkan_ctx* h = items[i].h;
+    if (int st = flush_pending(h)) return st;
+    ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  {
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    for (int dt = 0; dt < 3; ++dt)
+      if (int st = batch_run_group(dt, pb[dt], items, stream)) return st;
+  }
+  for (int i = 0; i < count; ++i) {
+    orkan_ctx* h = items[i].h;
+    h->n_launches += 1;
+    h->n_ops += items[i].nops;
+    if (items[i].init == ORKAN_INIT_PURE || items[i].init == ORKAN_BATCH_PAULI_SUM) {
+      reset_labels(h);
+      h->picture = items[i].init == ORKAN_INIT_PURE ? ORKAN_STATE : ORKAN_OBSERVABLE;
+    }
+  }
+  for (int i = 0; i < count; ++i)
+    if (items[i].status != ORKAN_OK)
+      return batch_fail(i, items[i].status, items[i].status == ORKAN_EZEROPROB
+                                                ? "a measurement outcome had probability <= 1e-300"
+                                                : "the gang barrier's time limit ran out");
   return ORKAN_OK;
 }

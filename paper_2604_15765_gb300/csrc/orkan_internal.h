@@ -121,6 +121,66 @@ struct PackedDesc {
 };
 cudaError_t launch_packed(int dtype, void* state, const PackedDesc& d, cudaStream_t stream);
 
+// Batched circuits (orkan_run_batch): one persistent launch runs the whole
+// circuits of many small operators, CTAs taking work slots from a device
+// queue; a request runs on `gang` consecutive slots (shared memory when the
+// gang is 1 and the array fits).  Op forms:
+//   BF_PTM1   : k = 1, coefficients R / 2 (4 x 4 real Pauli transfer matrix)
+//   BF_KRAUS2 : k = 2, r terms of 16 complex entries (row-major, re / im slots)
+//   BF_KRAUS3 : k = 3, r terms of 64 complex entries
+//   BF_MEASURE: Z measurement of q[0] with draw u, Born renormalisation
+//   BF_PROJECT: Pi_outcome (.) Pi_outcome, no renormalisation
+constexpr int kBatchThreads = 256;
+enum BatchForm : int32_t { BF_PTM1 = 0, BF_KRAUS2 = 1, BF_KRAUS3 = 2, BF_MEASURE = 3, BF_PROJECT = 4 };
+struct BatchOp {
+  int32_t form;
+  int32_t r;         // Kraus terms
+  int32_t q[3];      // physical qubits, ascending
+  int32_t coef;      // first 8-byte coefficient slot
+  int32_t meas;      // BF_MEASURE: index of its outcome / probability within the request
+  int32_t outcome;   // BF_PROJECT
+  double u;          // BF_MEASURE: uniform draw
+};
+struct BatchItem {
+  uint64_t state;      // device address of the tiled array
+  int64_t stored;      // stored elements
+  int64_t init_off;    // aux byte offset of the initial data (init 1: N complex; init 2: term table)
+  int64_t pauli_off;   // aux byte offset of the readout strings (3 uint64 masks x, z, y each)
+  int64_t psi_off;     // aux byte offset of the readout vector (N complex), or -1
+  int64_t part_off;    // first double of the gang's scratch partial sums
+  int32_t n, m;
+  int32_t init;        // 0: the array as it is, 1: pure state, 2: Pauli sum
+  int32_t nterms;      // init 2
+  int32_t op_begin, op_end;
+  int32_t npauli;
+  int32_t res;         // first result slot (2 per string, then <psi|H|psi>)
+  int32_t meas_base;   // first outcome / probability slot
+  int32_t gang;        // CTAs working on the request
+  int32_t first_slot;  // its first work slot
+  int32_t smem;        // 1: staged in shared memory (gang 1)
+  int32_t part_stride; // doubles of scratch per gang member
+  int32_t pad;
+};
+struct BatchDesc {
+  const BatchItem* items;
+  const BatchOp* ops;
+  const double* coef;
+  const unsigned char* aux;
+  const int32_t* slot_item;  // work slot -> request
+  int32_t* counter;          // queue head (zero at launch)
+  int32_t* bar;              // per request: barrier arrivals (zero at launch)
+  int32_t* status;           // per request: ORKAN_OK, ORKAN_EZEROPROB or ORKAN_ETIMEOUT (zero at launch)
+  double* partials;
+  double* results;
+  int32_t* outcomes;
+  double* probs;
+  uint64_t wait_ns;          // time limit of one gang barrier
+  int32_t nslots;
+  int32_t pad;
+};
+cudaError_t launch_batch(int dtype, const BatchDesc& d, int grid, size_t smem, cudaStream_t stream);
+cudaError_t batch_occupancy(int dtype, size_t smem, int* per_sm);
+
 // Record the message that orkan_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
 

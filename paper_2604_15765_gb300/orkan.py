@@ -19,6 +19,7 @@ ORKAN_C128, ORKAN_C64, ORKAN_DF64 = 0, 1, 2
 ORKAN_STATE, ORKAN_OBSERVABLE = 0, 1
 ORKAN_INIT_ZERO, ORKAN_INIT_MAXMIXED, ORKAN_INIT_DENSE, ORKAN_INIT_PURE = 0, 1, 2, 3
 ORKAN_OK, ORKAN_EINVAL, ORKAN_ENOMEM, ORKAN_ECUDA, ORKAN_EZEROPROB, ORKAN_EPICTURE, ORKAN_ENODEV = 0, -1, -2, -3, -4, -5, -6
+ORKAN_ETIMEOUT = -7
 DTYPES = {"c128": ORKAN_C128, "c64": ORKAN_C64, "df64": ORKAN_DF64}
 
 
@@ -42,6 +43,16 @@ class OrkanOp(C.Structure):
                 ("param", C.c_double), ("mats", C.POINTER(C.c_double))]
 
 
+class OrkanBatchItem(C.Structure):
+    """orkan_batch_item of include/orkan.h."""
+    _fields_ = [("h", C.c_void_p), ("init", C.c_int), ("init_data", C.POINTER(C.c_double)), ("nterms", C.c_int),
+                ("terms", C.c_char_p), ("coeffs", C.POINTER(C.c_double)), ("nops", C.c_int),
+                ("ops", C.POINTER(OrkanOp)), ("npaulis", C.c_int), ("paulis", C.c_char_p),
+                ("psi", C.POINTER(C.c_double)), ("out", C.POINTER(C.c_double)), ("outcomes", C.POINTER(C.c_int)),
+                ("probs", C.POINTER(C.c_double)), ("gang", C.c_int), ("status", C.c_int)]
+
+
+ORKAN_BATCH_KEEP, ORKAN_BATCH_PAULI_SUM = -1, 4
 ORKAN_OP_UNITARY, ORKAN_OP_KRAUS, ORKAN_OP_DEPOLARIZE, ORKAN_OP_DEPHASE = 0, 1, 2, 3
 ORKAN_OP_AMPDAMP, ORKAN_OP_MEASURE, ORKAN_OP_PROJECT = 4, 5, 6
 _i64 = C.c_int64
@@ -107,6 +118,8 @@ _SIGS = {
     "orkan_packed_depolarize": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p]),
     "orkan_packed_from_tiled": (C.c_int, [_h, C.c_void_p]),
     "orkan_packed_to_tiled": (C.c_int, [_h, C.c_void_p]),
+    "orkan_run_batch": (C.c_int, [C.c_int, C.POINTER(OrkanBatchItem), C.c_void_p]),
+    "orkan_batch_limits": (C.c_int, [C.c_int, C.c_double]),
     "orkan_checkpoint_bytes": (C.c_size_t, [_h]),
     "orkan_checkpoint_save": (C.c_int, [_h, C.c_void_p, C.c_size_t]),
     "orkan_checkpoint_load": (C.c_int, [_h, C.c_void_p, C.c_size_t]),
@@ -246,6 +259,22 @@ def orkan_load_tiled_async(h, host_buf: np.ndarray, picture: int = ORKAN_STATE):
 def orkan_store_tiled(h, host_buf: np.ndarray):
     assert host_buf.flags["C_CONTIGUOUS"]
     _check(_lib.orkan_store_tiled(h, host_buf.ctypes.data_as(C.c_void_p)), "orkan_store_tiled")
+
+
+def orkan_run_batch(items, stream_ptr=None):
+    """Run an array of OrkanBatchItem in one call; returns the per-item
+    statuses (ORKAN_OK, ORKAN_EZEROPROB, ORKAN_ETIMEOUT).  Validation errors
+    raise OrkanError before anything runs."""
+    arr = (OrkanBatchItem * len(items))(*items)
+    st = _lib.orkan_run_batch(len(items), arr, C.c_void_p(stream_ptr or 0))
+    statuses = [int(arr[i].status) for i in range(len(items))]
+    if st != ORKAN_OK and not (st in (ORKAN_EZEROPROB, ORKAN_ETIMEOUT) and st in statuses):
+        _check(st, "orkan_run_batch")
+    return statuses
+
+
+def orkan_batch_limits(max_ctas: int = 0, wait_seconds: float = 1.0):
+    _check(_lib.orkan_batch_limits(max_ctas, wait_seconds), "orkan_batch_limits")
 
 
 ORKAN_CKPT_HEADER_BYTES = 320
