@@ -386,7 +386,7 @@ def _request_errors(reqs, res, ref):
     return out
 
 
-def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=True):
+def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=True, batch_max_n=9):
     """Continuous batching vs one-at-a-time plain FP64 on the same requests.
     The plain arm runs every request alone, one pass per op, in native FP64
     (c64 requests too); its results are the reference for every served arm's
@@ -397,21 +397,24 @@ def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=
     arrival order (fifo) and shortest-estimated-work first (sjf)."""
     from paper_2604_15765_gb300 import serving
     out = {"requests": len(reqs), "slots": slots, "memory_budget_bytes": budget,
-           "served_form": "8 concurrent slots, fused passes (8 ops, composed)"}
+           "served_form": f"{slots} concurrent slots, fused passes (8 ops, composed); *_batched: requests of "
+                          f"n <= {batch_max_n} in persistent batched launches (orkan_run_batch) beside the slots; "
+                          "latency runs on the c128 batched form"}
     ref = None
     if baseline:
         ref, b = serving.serve(reqs, budget, slots=1, dtype_map={"c64": "c128"}, fusion=1, compose=False,
                                realtime=False)
         out["plain_fp64_one_at_a_time"] = b
-    arms = (("c128", {}), ("df64", {"c128": "df64"}))
+    arms = (("c128", {}, None), ("c128_batched", {}, batch_max_n), ("df64", {"c128": "df64"}, None),
+            ("df64_batched", {"c128": "df64"}, batch_max_n))
     cap = None
-    for label, dmap in arms:
-        res, st = serving.serve(reqs, budget, slots=slots, dtype_map=dmap, realtime=False)
-        st["c128_requests_in"] = label
+    for label, dmap, bmax in arms:
+        res, st = serving.serve(reqs, budget, slots=slots, dtype_map=dmap, realtime=False, batch_max_n=bmax)
+        st["c128_requests_in"] = label.split("_")[0]
         if ref is not None:
             st.update(_request_errors(reqs, res, ref))
         out[f"served_capacity_{label}"] = st
-        if cap is None:
+        if label == "c128_batched":
             cap = st
     out["served_capacity"] = cap
     base_t = [r["t"] for r in reqs]
@@ -419,9 +422,9 @@ def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=
         rate = frac * cap["solves_per_s"]
         span = base_t[-1] if base_t[-1] > 0 else 1.0
         scaled = [dict(r, t=r["t"] * (len(reqs) / rate) / span) for r in reqs]
-        _, st = serving.serve(scaled, budget, slots=slots, realtime=True)
+        _, st = serving.serve(scaled, budget, slots=slots, realtime=True, batch_max_n=batch_max_n)
         out[f"served_at_{frac:.1f}x_capacity"] = st
-        _, st = serving.serve(scaled, budget, slots=slots, realtime=True, policy="sjf")
+        _, st = serving.serve(scaled, budget, slots=slots, realtime=True, policy="sjf", batch_max_n=batch_max_n)
         out[f"served_at_{frac:.1f}x_capacity_sjf"] = st
     torch.cuda.synchronize()
     return out

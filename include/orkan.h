@@ -318,8 +318,8 @@ int orkan_run_circuit(orkan_h h, int count, const orkan_op *ops, int *outcomes, 
  *   out     host: npaulis values tr(P H), then <psi|H|psi> if psi.
  *   outcomes, probs  host, one per MEASURE op (either may be NULL).
  *   gang    0: automatic (1 when the array fits shared memory, else about
- *           one CTA per 32 Ki stored elements, at most 64); else the number
- *           of CTAs to use (1..64).
+ *           one CTA per 8 Ki (C128) or 32 Ki (C64, DF64) stored elements, at
+ *           most 64); else the number of CTAs to use (1..64).
  *   status  written by the call: ORKAN_OK, ORKAN_EZEROPROB (a measurement
  *           outcome had probability <= 1e-300; the item stopped there) or
  *           ORKAN_ETIMEOUT (its gang did not assemble within the wait limit,

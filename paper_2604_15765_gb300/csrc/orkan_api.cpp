@@ -2140,7 +2140,10 @@ int batch_pack_item(const orkan_batch_item& it, int idx, PackedBatch* pb) {
   // gang and placement
   const size_t bytes = h->bytes;
   int G = it.gang;
-  if (G == 0) G = bytes <= kBatchSmemCap ? 1 : int(std::min<int64_t>(64, std::max<int64_t>(2, (I.stored + 32767) / 32768)));
+  // automatic gangs: about 8 Ki stored elements per CTA in native FP64 (GB300's
+  // FP64 pipe does 2 operations per SM per clock), 32 Ki on the FP32 pipe
+  const int64_t per_cta = dtype == DT_C128 ? 8192 : 32768;
+  if (G == 0) G = bytes <= kBatchSmemCap ? 1 : int(std::min<int64_t>(64, std::max<int64_t>(2, (I.stored + per_cta - 1) / per_cta)));
   I.gang = G;
   I.smem = (G == 1 && bytes <= kBatchSmemCap) ? 1 : 0;
   if (I.smem) pb->smem = std::max(pb->smem, (bytes + 15) & ~size_t(15));

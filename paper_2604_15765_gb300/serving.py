@@ -116,63 +116,134 @@ def run_request(pool: HandlePool, req, dtype_map=None, fusion=8, compose=True):
     return out
 
 
+def batch_item(pool: HandlePool, req, dtype_map=None):
+    """One request as an orkan_run_batch item on a pooled handle (the whole
+    circuit and its readouts in the batched launch): Schroedinger from the
+    product state psi0, returning the Pauli expectations; Heisenberg from the
+    Pauli sum, the adjoint circuit in reverse order, returning
+    <psi0|O|psi0> = tr(O rho0)."""
+    dtype = (dtype_map or {}).get(req["dtype"], req["dtype"])
+    (h,) = pool.acquire(req["n"], dtype, 1)
+    if req["picture"] == "schrodinger":
+        item = {"h": h, "init": "pure", "psi0": req["psi0"], "ops": req["ops"], "paulis": req["paulis"]}
+    else:
+        item = {"h": h, "init": "pauli_sum", "terms": req["paulis"], "coeffs": req["coeffs"],
+                "ops": list(reversed(req["ops"])), "psi": req["psi0"]}
+    return item, (req["n"], dtype, h)
+
+
+def run_batched(pool: HandlePool, reqs, dtype_map=None):
+    """Run requests in one orkan_run_batch call; returns their result vectors."""
+    items, held = [], []
+    try:
+        for r in reqs:
+            it, hd = batch_item(pool, r, dtype_map)
+            items.append(it)
+            held.append(hd)
+        res = circuit.run_batch(items)
+    finally:
+        for n, dt, h in held:
+            pool.release(n, dt, [h])
+    for r, x in zip(reqs, res):
+        if x["status"] != ok.ORKAN_OK:
+            raise ok.OrkanError(x["status"], "serve", f"request {r['id']} failed in the batched launch")
+    return [x["out"] for x in res]
+
+
 def request_cost(req) -> float:
     """Estimated device work of a request: ops x stored elements (~4^n)."""
     return float(len(req["ops"])) * 4.0 ** req["n"]
 
 
 def serve(requests, budget_bytes, slots=8, dtype_map=None, fusion=8, compose=True, realtime=True,
-          tile_log2=5, policy="fifo"):
+          tile_log2=5, policy="fifo", batch_max_n=None, batch_size=256):
     """Continuous batching: requests become eligible at their arrival time
     (offsets from the start when ``realtime``), are admitted when a slot is
     free and their bytes fit the budget, and run concurrently.  ``policy``
     orders the eligible requests: "fifo" by arrival, "sjf" shortest estimated
-    work first (``request_cost``; ties by arrival).  Returns (results by
-    request id, stats)."""
+    work first (``request_cost``; ties by arrival).  With ``batch_max_n``,
+    requests of at most that many qubits do not take a slot: one more worker
+    collects every eligible one (up to ``batch_size``, within half the memory
+    budget) into a single orkan_run_batch launch, again and again, while
+    larger requests run on the slots.  Returns (results by request id,
+    stats)."""
     if policy not in ("fifo", "sjf"):
         raise ValueError(policy)
     pool = HandlePool(budget_bytes, tile_log2)
     order = sorted(requests, key=lambda r: r["t"])
-    arrived = [0]          # requests of `order` moved to the eligible heap so far
-    eligible = []          # (key, seq, request)
+    arrived = [0]          # requests of `order` moved to an eligible heap so far
+    eligible = [[], []]    # (key, seq, request): [0] slot requests, [1] batched requests
     qlock = threading.Lock()
     results, lat = {}, {}
     errors = []
     t0 = time.perf_counter()
 
-    def take():
-        """The next request to run, or None when every request has been taken."""
+    def small(r):
+        return batch_max_n is not None and r["n"] <= batch_max_n
+
+    def admit(now):
+        while arrived[0] < len(order) and (not realtime or order[arrived[0]]["t"] <= now):
+            r = order[arrived[0]]
+            key = request_cost(r) if policy == "sjf" else r["t"]
+            heapq.heappush(eligible[1 if small(r) else 0], (key, arrived[0], r))
+            arrived[0] += 1
+
+    def take(which, count):
+        """Up to `count` eligible requests of one kind ([] when none will come)."""
         while True:
             with qlock:
                 now = time.perf_counter() - t0
-                while arrived[0] < len(order) and (not realtime or order[arrived[0]]["t"] <= now):
-                    r = order[arrived[0]]
-                    key = request_cost(r) if policy == "sjf" else r["t"]
-                    heapq.heappush(eligible, (key, arrived[0], r))
-                    arrived[0] += 1
-                if eligible:
-                    return heapq.heappop(eligible)[2]
+                admit(now)
+                if eligible[which]:
+                    out, mem = [], 0
+                    while eligible[which] and len(out) < count:
+                        r = eligible[which][0][2]
+                        need = pool.nbytes(r["n"], (dtype_map or {}).get(r["dtype"], r["dtype"]))
+                        if out and mem + need > budget_bytes // 2:
+                            break
+                        heapq.heappop(eligible[which])
+                        out.append(r)
+                        mem += need
+                    return out
                 if arrived[0] >= len(order):
-                    return None
+                    return []
                 wait = order[arrived[0]]["t"] - now
             time.sleep(max(wait, 0.0))
 
+    def done(req, res):
+        t = time.perf_counter()
+        results[req["id"]] = res
+        lat[req["id"]] = t - (t0 + req["t"] if realtime else t0)
+
     def worker():
         while True:
-            req = take()
-            if req is None:
+            got = take(0, 1)
+            if not got:
                 return
-            arrival = t0 + req["t"] if realtime else t0
+            req = got[0]
             try:
                 res = run_request(pool, req, dtype_map, fusion, compose)
             except Exception as e:  # noqa: BLE001  (reported to the caller)
                 errors.append((req["id"], repr(e)))
                 continue
-            done = time.perf_counter()
-            results[req["id"]] = res
-            lat[req["id"]] = done - arrival
+            done(req, res)
+
+    def batch_worker():
+        while True:
+            got = take(1, batch_size)
+            if not got:
+                return
+            try:
+                res = run_batched(pool, got, dtype_map)
+            except Exception as e:  # noqa: BLE001
+                errors.append((got[0]["id"], repr(e)))
+                continue
+            for r, x in zip(got, res):
+                done(r, x)
 
     threads = [threading.Thread(target=worker, daemon=True) for _ in range(slots)]
+    if batch_max_n is not None:
+        threads.append(threading.Thread(target=batch_worker, daemon=True))
     for t in threads:
         t.start()
     for t in threads:
@@ -185,5 +256,6 @@ def serve(requests, budget_bytes, slots=8, dtype_map=None, fusion=8, compose=Tru
     ops = sum(len(r["ops"]) for r in requests)
     stats = {"requests": len(results), "elapsed_s": elapsed, "solves_per_s": len(results) / elapsed,
              "ops_per_s": ops / elapsed, "p50_ms": float(np.percentile(lv, 50) * 1e3),
-             "p99_ms": float(np.percentile(lv, 99) * 1e3), "slots": slots, "policy": policy}
+             "p99_ms": float(np.percentile(lv, 99) * 1e3), "slots": slots, "policy": policy,
+             "batch_max_n": batch_max_n}
     return results, stats

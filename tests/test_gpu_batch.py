@@ -174,11 +174,10 @@ def test_zero_probability_and_gang_time_limit():
 def test_invalid_items_are_refused_before_launch():
     h = ok.orkan_alloc(4, ok.ORKAN_C128, 5)
     try:
-        terms, coeffs = ["XZII", "IIYY"], [0.5, -1.0]
-        with pytest.raises(ok.OrkanError) as e:
-            circuit.run_batch([{"h": h, "init": "pauli_sum", "terms": terms, "coeffs": coeffs,
-                                "ops": [S.op_measure(1, 0.5)]}])
-        assert e.value.status == ok.ORKAN_EINVAL or e.value.status == ok.ORKAN_EPICTURE
+        ok.orkan_init_observable(h, ["XZII", "IIYY"], [0.5, -1.0])
+        with pytest.raises(ok.OrkanError) as e:   # a MEASURE op on the kept observable
+            circuit.run_batch([{"h": h, "init": "keep", "picture": "schrodinger", "ops": [S.op_measure(1, 0.5)]}])
+        assert e.value.status == ok.ORKAN_EPICTURE
         with pytest.raises(ok.OrkanError) as e:
             circuit.run_batch([{"h": h, "init": "pure", "psi0": np.ones(16) / 4,
                                 "ops": [S.op_unitary(np.eye(2), [4])]}])

@@ -33,9 +33,22 @@ def test_results_same_alone_and_in_the_mix(policy):
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
 
 
-def test_served_results_match_oracle():
+def test_batched_results_same_alone_and_in_the_mix():
+    """With the batched launch for n <= 7, a request served alone (a batch of
+    one, or a slot for n > 7) gives the bits it gives in the mix."""
+    reqs = _requests()
+    budget = 2 << 30
+    mixed, stats = serving.serve(reqs, budget, slots=4, realtime=True, batch_max_n=7)
+    assert stats["requests"] == len(reqs)
+    for r in reqs:
+        alone, _ = serving.serve([dict(r, t=0.0)], budget, slots=1, realtime=False, batch_max_n=7)
+        assert np.array_equal(alone[r["id"]], mixed[r["id"]]), r["id"]
+
+
+@pytest.mark.parametrize("batch_max_n", [None, 9])
+def test_served_results_match_oracle(batch_max_n):
     reqs = _requests(12)
-    res, _ = serving.serve(reqs, 1 << 30, slots=4, realtime=False)
+    res, _ = serving.serve(reqs, 1 << 30, slots=4, realtime=False, batch_max_n=batch_max_n)
     for r in reqs:
         tol = 1e-10 if r["dtype"] == "c128" else 2e-4
         psi = r["psi0"]
