@@ -466,6 +466,23 @@ def _run_timed(ok, circuit, torch, stream, n, dt, m, fusion, compose, ops, pauli
     return h, st, exps
 
 
+def small_request_study(S, torch, count=600, budget=8 << 30):
+    """Requests of n = 4..10 (the serving mix's small end, where every op is
+    launch-bound): solves/s with the slots alone, and with the batched
+    persistent launch for n <= 9 beside them; same requests, own dtypes."""
+    from paper_2604_15765_gb300 import serving
+    reqs = S.serving_stream(count=count, seed=S.BASE_SEED + 14, n_range=(4, 10))
+    out = {"requests": count, "n_range": [4, 10]}
+    res = {}
+    for label, bmax in (("slots_only", None), ("batched_n_le_9", 9)):
+        res[label], st = serving.serve(reqs, budget, slots=8, realtime=False, batch_max_n=bmax)
+        out[label] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
+    out.update({"batched_" + k: v for k, v in _request_errors(reqs, res["batched_n_le_9"], res["slots_only"]).items()})
+    out["speedup_solves_per_s"] = round(out["batched_n_le_9"]["solves_per_s"] / out["slots_only"]["solves_per_s"], 2)
+    torch.cuda.synchronize()
+    return out
+
+
 def sweep_elements(ok, circuit, wl, n, m, dt, fusion, compose, stream, sample=None):
     """One Schroedinger sweep from the bench's initial state (the Haar pure
     state depolarised on every qubit) in the given form; returns sampled
@@ -1040,6 +1057,7 @@ def main(argv=None):
         per_op = per_op_table(ok, wl, n, m, ("df64", "c128", "c64"), stream, torch)
         from workloads import synth as S
         serving_res = serving_study(S.serving_stream(count=args.serve_requests), torch, budget=32 << 30)
+        serving_res["small_requests"] = small_request_study(S, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
