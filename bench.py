@@ -934,8 +934,17 @@ def main(argv=None):
     if args.workload == "serving":
         from workloads import synth as S
         reqs = S.serving_stream(count=5000)
-        st = serving_study(reqs, torch, budget=64 << 30, realtime_fracs=(0.5, 0.9, 1.2))
-        cap = st["served_capacity"]
+        if world > 1:
+            # request-level replicas: each rank serves its routed share on its own GPU, nothing is
+            # exchanged while requests run; results and latencies are gathered once at the end
+            from paper_2604_15765_gb300 import serving
+            _, cap = serving.serve_replicated(reqs, 64 << 30, slots=8, realtime=False, batch_max_n=9)
+            st = {"replicated_capacity": cap}
+        else:
+            st = serving_study(reqs, torch, budget=64 << 30, realtime_fracs=(0.5, 0.9, 1.2))
+            cap = st["served_capacity"]
+        if rank != 0:
+            return 0
         line = {"metric": METRIC, "value": round(cap["ops_per_s"], 2), "unit": UNIT, "n_gpus": world, "steps": 1,
                 "warmup": 0, "ms_per_step": round(cap["elapsed_s"] * 1e3, 1), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "c128/c64 requests, each at its own dtype",

@@ -156,7 +156,7 @@ def request_cost(req) -> float:
 
 
 def serve(requests, budget_bytes, slots=8, dtype_map=None, fusion=8, compose=True, realtime=True,
-          tile_log2=5, policy="fifo", batch_max_n=None, batch_size=256):
+          tile_log2=5, policy="fifo", batch_max_n=None, batch_size=256, latencies=False):
     """Continuous batching: requests become eligible at their arrival time
     (offsets from the start when ``realtime``), are admitted when a slot is
     free and their bytes fit the budget, and run concurrently.  ``policy``
@@ -166,7 +166,9 @@ def serve(requests, budget_bytes, slots=8, dtype_map=None, fusion=8, compose=Tru
     collects every eligible one (up to ``batch_size``, within half the memory
     budget) into a single orkan_run_batch launch, again and again, while
     larger requests run on the slots.  Returns (results by request id,
-    stats)."""
+    stats); with ``latencies`` the stats also list every request's latency.
+    One replica on one GPU; ``serve_replicated`` spreads requests over
+    torch.distributed ranks."""
     if policy not in ("fifo", "sjf"):
         raise ValueError(policy)
     pool = HandlePool(budget_bytes, tile_log2)
@@ -258,4 +260,72 @@ def serve(requests, budget_bytes, slots=8, dtype_map=None, fusion=8, compose=Tru
              "ops_per_s": ops / elapsed, "p50_ms": float(np.percentile(lv, 50) * 1e3),
              "p99_ms": float(np.percentile(lv, 99) * 1e3), "slots": slots, "policy": policy,
              "batch_max_n": batch_max_n}
+    if latencies:
+        stats["latencies_s"] = [float(x) for x in lv] if lat else []
     return results, stats
+
+
+# ------------------------------------------------------------------ request-level replicas
+def route(requests, world: int):
+    """Spread requests over `world` independent replicas (one GPU each): each
+    request, in decreasing estimated work (ties by id), goes to the replica
+    with the least work so far (ties by rank).  Deterministic, so every rank
+    computes the same assignment without communicating.  Returns one request
+    list per rank, each in arrival order."""
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for r in sorted(requests, key=lambda r: (-request_cost(r), r["id"])):
+        k = min(range(world), key=lambda w: (load[w], w))
+        parts[k].append(r)
+        load[k] += request_cost(r)
+    return [sorted(p, key=lambda r: (r["t"], r["id"])) for p in parts]
+
+
+def merge_replicas(parts):
+    """Combine the (results, stats) of every replica: results by request id;
+    solves/s and ops/s = all requests / the slowest replica's elapsed time;
+    p50/p99 over every request's latency (each replica reports its own)."""
+    results = {}
+    lat = []
+    elapsed = 0.0
+    nreq = 0
+    ops = 0.0
+    for res, st, lats in parts:
+        results.update(res)
+        lat.extend(lats)
+        elapsed = max(elapsed, st["elapsed_s"])
+        nreq += st["requests"]
+        ops += st["ops_per_s"] * st["elapsed_s"]
+    lv = np.array(sorted(lat)) if lat else np.zeros(1)
+    return results, {"requests": nreq, "replicas": len(parts), "elapsed_s": elapsed,
+                     "solves_per_s": nreq / elapsed if elapsed > 0 else 0.0,
+                     "ops_per_s": ops / elapsed if elapsed > 0 else 0.0,
+                     "p50_ms": float(np.percentile(lv, 50) * 1e3), "p99_ms": float(np.percentile(lv, 99) * 1e3)}
+
+
+def serve_replicated(requests, budget_bytes, group=None, serve_fn=None, **kw):
+    """Request-level data parallelism: under torch.distributed every rank
+    serves its share (``route``) on its own GPU as an independent replica --
+    nothing is exchanged while requests run -- and the ranks gather their
+    results and latencies once at the end.  Without an initialised process
+    group this is ``serve``.  ``serve_fn`` (default ``serve``) must return
+    (results, stats) with stats["latencies_s"]."""
+    import torch.distributed as dist
+    serve_fn = serve_fn or _serve_with_latencies
+    if not (dist.is_available() and dist.is_initialized()):
+        res, st = serve_fn(requests, budget_bytes, **kw)
+        return merge_replicas([(res, st, st.pop("latencies_s"))])
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    mine = route(requests, world)[rank]
+    res, st = serve_fn(mine, budget_bytes, **kw)
+    lats = st.pop("latencies_s")
+    gathered = [None] * world
+    dist.all_gather_object(gathered, (res, st, lats), group=group)
+    return merge_replicas(gathered)
+
+
+def _serve_with_latencies(requests, budget_bytes, **kw):
+    if not requests:
+        return {}, {"requests": 0, "elapsed_s": 0.0, "ops_per_s": 0.0, "latencies_s": []}
+    res, st = serve(requests, budget_bytes, latencies=True, **kw)
+    return res, st
