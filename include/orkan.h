@@ -142,6 +142,21 @@ int orkan_set_stream(orkan_h h, void *cuda_stream);
  * max_ops = 1 with compose = 0 is the plain one-pass-per-op path. */
 int orkan_set_fusion(orkan_h h, int max_ops, int compose);
 
+/* Tensor-core passes for in-tile runs (complex64 handles with tile_log2 = 5;
+ * no counterpart in the paper, which applies ops one by one).  A run of
+ * consecutive single-Kraus ops (unitaries, or one-operator Kraus sets) on
+ * qubits below the tile size is, as a whole, one operator L_blk on the tile's
+ * 5 qubits (composed in FP64 on the host); it maps every stored tile T to
+ * L_blk T L_blk^dagger (Eq. 2 with k = m, Sec. III-C intra-tile case), two
+ * dense complex 32 x 32 x 32 products per tile whatever the run's length,
+ * run on tcgen05 tensor cores with split-TF32 operands (about 2^-22 relative
+ * per pass; complex64 storage holds 2^-24).  Such a run then holds up to 64
+ * ops instead of the fusion depth.  mode 0: off (default); 1: runs with at
+ * least two dense two-qubit ops or at least six ops; 2: every such run.
+ * Other handles and ops are unaffected.  A bounded wait inside the pass that
+ * runs out makes the next orkan_sync return ORKAN_ETIMEOUT.  Errors: EINVAL. */
+int orkan_set_tensor(orkan_h h, int mode);
+
 int orkan_get_info(orkan_h h, int *n, int *dtype, int *tile_log2, int *picture);
 
 /* Autotuner: the tile size (tile_log2, 3..5) and fusion depth (max_ops,

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liborkan_gb300.so")
 SOURCES = ["pass_df64.cu", "pass_df64_p2.cu", "pass_f64.cu", "pass_f64_p2.cu", "pass_f32.cu", "pass_f32_p2.cu",
            "pass_dispatch.cu", "aux_kernels.cu", "k3_kernels.cu", "packed_kernels.cu", "orkan_api.cpp", "noalloc.cu", "probe.cu",
-           "batch_kernels.cu"]
+           "batch_kernels.cu", "tc_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

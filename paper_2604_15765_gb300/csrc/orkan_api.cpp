@@ -140,6 +140,11 @@ struct HostOp {
   std::vector<double> R;       // single-qubit ops: full 4x4 PTM (for composition)
   std::vector<double> coef;    // kind-specific FP64 coefficients (2- and 3-qubit ops)
   std::vector<long long> codes;  // monomial ops: permutation and phase codes
+  // single-Kraus ops (k <= 2): the map is L (.) L^dagger with L on q[] (bit l of
+  // L's index on q[l]), the adjoint already applied on observables; consecutive
+  // in-tile ones compose into one block for the tensor-core pass
+  Mat L;
+  bool has_L = false;
 };
 
 // A unitary is monomial with quarter-turn phases when every row holds exactly
@@ -235,6 +240,8 @@ struct orkan_ctx {
   int phys[64];            // qubit relabelling: logical qubit -> physical bit position
   int cap_phys[64];        // the map when the running graph capture began
   int auto_relabel = 0;    // 1: orkan_run_circuit moves a circuit's most used qubits into the tile
+  int tc_mode = 0;              // tensor-core pass for composed in-tile runs: 0 off, 1 auto, 2 always
+  int32_t* d_err = nullptr;     // device error word of the tensor-core pass (allocated on first use)
   std::vector<cudaEvent_t> ev_free;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
 };
@@ -299,8 +306,12 @@ int slots_upper_bound(const orkan_ctx* h, const HostOp& op) {
   return op.nq == 1 ? coef_slots(OP_PTM1, paired) : coef_slots(op.kind, paired);
 }
 
+bool tc_run(const orkan_ctx* h);
+bool tc_op_ok(const orkan_ctx* h, const HostOp& op);
+
 bool fits(const orkan_ctx* h, const HostOp& op) {
   if (h->pending.empty()) return true;
+  if (tc_run(h) && tc_op_ok(h, op)) return true;   // the run stays one composed block
   if (int(h->pending.size()) >= std::min(h->fusion, kMaxOps)) return false;
   const PassShape s = shape_of(h, h->pending, &op);
   if (s.nh > 2) return false;
@@ -416,8 +427,70 @@ int run_k3(orkan_ctx* h, const HostOp& op) {
   return ORKAN_OK;
 }
 
+// ------------------------------------------------------------------ tensor-core pass
+constexpr int kTcMaxOps = 64;
+
+bool tc_op_ok(const orkan_ctx* h, const HostOp& op) {
+  if (!op.has_L || op.nq > 2) return false;
+  for (int l = 0; l < op.nq; ++l)
+    if (op.q[l] >= h->g.m) return false;
+  return true;
+}
+// The pending run may become one tensor-core pass (every op in-tile with a single Kraus operator).
+bool tc_run(const orkan_ctx* h) {
+  if (h->tc_mode == 0 || h->dtype != DT_C64 || h->g.m != 5 || h->pending.empty()) return false;
+  for (const HostOp& op : h->pending)
+    if (!tc_op_ok(h, op)) return false;
+  return true;
+}
+// ... and is worth it: mode 2 always; mode 1 with two dense two-qubit ops or six ops.
+bool tc_take(const orkan_ctx* h) {
+  if (!tc_run(h)) return false;
+  if (h->tc_mode == 2) return true;
+  int dense2 = 0;
+  for (const HostOp& op : h->pending) dense2 += op.nq == 2 && op.codes.empty();
+  return dense2 >= 2 || h->pending.size() >= 6;
+}
+
+// L_blk = L_k ... L_1 over the run, each L embedded on the tile's m qubits (FP64).
+int flush_tc(orkan_ctx* h) {
+  const int M = 1 << h->g.m;
+  Mat blk(M * M, 0.0);
+  for (int i = 0; i < M; ++i) blk[i * M + i] = 1.0;
+  for (const HostOp& op : h->pending) {
+    const int d = 1 << op.nq;
+    int mask = 0;
+    for (int l = 0; l < op.nq; ++l) mask |= 1 << op.q[l];
+    auto loc = [&](int r) {
+      int a = 0;
+      for (int l = 0; l < op.nq; ++l) a |= ((r >> op.q[l]) & 1) << l;
+      return a;
+    };
+    Mat E(M * M, 0.0);
+    for (int r = 0; r < M; ++r)
+      for (int c = 0; c < M; ++c)
+        if ((r & ~mask) == (c & ~mask)) E[r * M + c] = op.L[loc(r) * d + loc(c)];
+    blk = matmul(E, blk, M);
+  }
+  TcDesc d;
+  d.ntiles = h->g.ntiles;
+  d.err = h->d_err;
+  for (int i = 0; i < M * M; ++i) d.u[i] = make_float2(float(blk[i].real()), float(blk[i].imag()));
+  const int64_t nops = int64_t(h->pending.size());
+  h->pending.clear();
+  std::pair<cudaEvent_t, cudaEvent_t> ev;
+  if (int st = timing_begin(h, &ev)) return st;
+  ORKAN_CUDA(launch_tc(h->d_state, d, h->stream));
+  if (int st = timing_end(h, ev, 0.0)) return st;
+  h->n_passes += 1;
+  h->n_ops += nops;
+  h->n_launches += 1;
+  return ORKAN_OK;
+}
+
 int flush_pending(orkan_ctx* h) {
   if (h->pending.empty()) return ORKAN_OK;
+  if (tc_take(h)) return flush_tc(h);
   const PassShape s = shape_of(h, h->pending, nullptr);
   // in-tile passes run with four independent tiles per work item, on the
   // one-high-qubit group geometry
@@ -491,6 +564,8 @@ int enqueue(orkan_ctx* h, HostOp op) {
     HostOp& last = h->pending.back();
     if (last.nq == 1 && last.q[0] == op.q[0]) {
       last.R = mat4mul(op.R, last.R);
+      if (last.has_L && op.has_L) last.L = matmul(op.L, last.L, 2);
+      else last.has_L = false;
       last.codes.clear();
       if (!(last.kind == op.kind && (op.kind == OP_PTM1_U || op.kind == OP_PTM1_AD))) {
         last.kind = is_unitary_pattern(last.R) ? OP_PTM1_U : (is_ad_pattern(last.R) ? OP_PTM1_AD : OP_PTM1);
@@ -499,12 +574,16 @@ int enqueue(orkan_ctx* h, HostOp op) {
       return ORKAN_OK;
     }
   }
+  // a run longer than a fused pass holds can only leave as a tensor-core pass
+  if (!h->pending.empty() && int(h->pending.size()) > kMaxOps && !tc_op_ok(h, op))
+    if (int st = flush_pending(h)) return st;
   if (!fits(h, op)) {
     const int st = flush_pending(h);
     if (st != ORKAN_OK) return st;
   }
   h->pending.push_back(std::move(op));
-  if (int(h->pending.size()) >= std::min(h->fusion, kMaxOps)) return flush_pending(h);
+  const int limit = tc_run(h) ? kTcMaxOps : std::min(h->fusion, kMaxOps);
+  if (int(h->pending.size()) >= limit) return flush_pending(h);
   return ORKAN_OK;
 }
 
@@ -592,6 +671,10 @@ int make_op_adj(bool adj, int k, const int* qubits, const std::vector<Mat>& krau
   if (k == 1) {
     op.q[0] = qubits[0];
     op.R = ptm(1, kraus, adj);
+    if (kraus.size() == 1) {
+      op.L = adj ? dagger(kraus[0], 2) : kraus[0];
+      op.has_L = true;
+    }
     std::vector<long long> pp, qq;
     if (unitary && monomial(adj ? dagger(kraus[0], 2) : kraus[0], 2, &pp, &qq)) {
       op.kind = OP_PTM1_U;   // composes as a unitary PTM if a neighbour merges into it
@@ -619,6 +702,8 @@ int make_op_adj(bool adj, int k, const int* qubits, const std::vector<Mat>& krau
     if (kraus.size() == 1) {
       // direct form h -> V h V^dagger (Eq. 2 with r = 1)
       const Mat V = adj ? dagger(kraus[0], 4) : kraus[0];
+      op.L = V;
+      op.has_L = true;
       std::vector<long long> pp, qq;
       op.kind = (unitary && monomial(V, 4, &pp, &qq)) ? OP_MONO2 : OP_U2;
       op.coef.resize(32);
@@ -770,6 +855,8 @@ int setup_handle(orkan_ctx* c) {
   if (cudaMalloc(&c->d_res, sizeof(double) * 4) != cudaSuccess) return fail(ORKAN_ENOMEM, "cudaMalloc(res) failed");
   if (cudaMallocHost(&c->h_res, sizeof(double) * 4) != cudaSuccess)
     return fail(ORKAN_ENOMEM, "cudaMallocHost(res) failed");
+  if (cudaMalloc(&c->d_err, sizeof(int32_t)) != cudaSuccess) return fail(ORKAN_ENOMEM, "cudaMalloc(err) failed");
+  ORKAN_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int32_t), c->stream));
   return ORKAN_OK;
 }
 
@@ -784,6 +871,7 @@ void release_handle(orkan_ctx* c) {
   if (c->d_upload) cudaFree(c->d_upload);
   if (c->d_partials) cudaFree(c->d_partials);
   if (c->d_res) cudaFree(c->d_res);
+  if (c->d_err) cudaFree(c->d_err);
   if (c->h_res) cudaFreeHost(c->h_res);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -991,6 +1079,14 @@ int orkan_set_stream(orkan_h h, void* cuda_stream) {
   }
   h->own_stream = false;
   h->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  return ORKAN_OK;
+}
+
+int orkan_set_tensor(orkan_h h, int mode) {
+  if (int st = check_handle(h)) return st;
+  if (mode < 0 || mode > 2) return fail(ORKAN_EINVAL, "mode must be 0, 1 or 2");
+  if (int st = flush_pending(h)) return st;
+  h->tc_mode = mode;
   return ORKAN_OK;
 }
 
@@ -1570,6 +1666,14 @@ int orkan_sync(orkan_h h) {
   if (int st = check_blocking(h)) return st;
   if (int st = flush_pending(h)) return st;
   ORKAN_CUDA(cudaStreamSynchronize(h->stream));
+  if (h->tc_mode) {
+    int32_t e = 0;
+    ORKAN_CUDA(cudaMemcpy(&e, h->d_err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e) {
+      ORKAN_CUDA(cudaMemset(h->d_err, 0, sizeof(e)));
+      return fail(ORKAN_ETIMEOUT, "tensor-core pass: an mbarrier wait ran out (the operator is undefined)");
+    }
+  }
   return ORKAN_OK;
 }
 

@@ -181,6 +181,17 @@ struct BatchDesc {
 cudaError_t launch_batch(int dtype, const BatchDesc& d, int grid, size_t smem, cudaStream_t stream);
 cudaError_t batch_occupancy(int dtype, size_t smem, int* per_sm);
 
+// Tensor-core pass (tc_kernels.cu): every stored tile T <- L T L^dagger for one
+// composed in-tile unitary L (m = 5, 32 x 32, complex64 storage), on tcgen05
+// MMAs.  u: L row-major as (re, im) floats; err: device word set to 1 if a
+// bounded wait ran out.  The matrix travels in the kernel parameter.
+struct TcDesc {
+  int64_t ntiles;
+  int32_t* err;
+  float2 u[32 * 32];
+};
+cudaError_t launch_tc(void* state, const TcDesc& d, cudaStream_t stream);
+
 // Record the message that orkan_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
 

@@ -1,0 +1,240 @@
+// Tensor-core conjugation of every stored tile by one composed in-tile block.
+//
+// A run of consecutive unitaries whose qubits all lie inside the tile (every
+// target below m, Sec. III-C's intra-tile case) is, as a whole, one unitary
+// L_blk on the tile's m qubits (composed on the host in FP64), and the run
+// maps every stored tile T -- diagonal or not -- to L_blk T L_blk^dagger
+// (Eq. 2 with k = m).  That is a dense complex contraction, two 32 x 32 x 32
+// products per tile at m = 5, independent of the run's length, so it goes to
+// the 5th-generation tensor cores:
+//
+//   GEMM 1 (A = T^T per tile, B = L^T):   Y^T = T^T L^T
+//   GEMM 2 (A = conj(Y) per tile, B = L^T): conj(T') = conj(Y) L^T,
+//                                          since T' = Y L^dagger
+//
+// Complex products run as real ones, [Cr Ci] = [Ar Ai] [[Br, Bi], [-Bi, Br]],
+// so one CTA step is a 128 x 64 x 64 real GEMM: four tiles (32 rows each) on
+// M = 128, real and imaginary parts on N = K = 64.  Both GEMMs share the same
+// B.  FP32 accuracy comes from the split-TF32 scheme: a = a_hi + a_lo with
+// a_hi = tf32(a), a_lo = tf32(a - a_hi), and A B ~ A_hi B_hi + A_hi B_lo +
+// A_lo B_hi (the dropped A_lo B_lo term is below 2^-22 relative).
+//
+// tcgen05.mma (kind::tf32, cta_group::1, M = 128, N = 64, K = 8 per
+// instruction) is issued by one thread; operands are K-major, no swizzle,
+// 8-row x 16-byte core matrices (leading byte offset 128 B along K, stride
+// byte offset 2048 B between 8-row groups); the FP32 accumulators live in
+// TMEM (128 lanes x 64 columns per GEMM) and come back with tcgen05.ld
+// 32x32b (thread t holds row t).  Completion is signalled by tcgen05.commit
+// on an mbarrier; every wait on it is bounded and sets an error word instead
+// of hanging.  complex64 storage (8-byte elements) at m = 5.
+#include <algorithm>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "orkan_internal.h"
+#include "device_util.cuh"
+
+namespace orkan {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr uint32_t kLbo = 128;                 // K-direction core-matrix stride
+constexpr uint32_t kSboA = 2048;               // 8-row group stride (16 K cores x 128 B)
+constexpr uint32_t kSboB = 2048;
+constexpr uint32_t kABytes = 128 * 64 * 4;     // one A operand (hi or lo): 32 KiB
+constexpr uint32_t kBBytes = 64 * 64 * 4;      // one B operand: 16 KiB
+constexpr uint32_t kSmemBytes = 2 * kABytes + 2 * kBBytes;   // 96 KiB
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(64 >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+constexpr long long kWaitLimit = 1 << 24;      // polls of one mbarrier phase before giving up
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo) {
+  return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t((kLbo >> 4) & 0x3FFF) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
+}
+
+// Byte offset of element (row, k) of a K-major operand (k < 64).
+__device__ __forceinline__ uint32_t koff(int row, int k, uint32_t sbo) {
+  return uint32_t(row >> 3) * sbo + uint32_t(k >> 2) * kLbo + uint32_t(row & 7) * 16 + uint32_t(k & 3) * 4;
+}
+
+__device__ __forceinline__ float tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// a -> (hi, lo) stored at byte offset off of the hi and lo operand buffers.
+__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, uint32_t off, float a) {
+  const float h = tf32(a);
+  *reinterpret_cast<float*>(hi + off) = h;
+  *reinterpret_cast<float*>(lo + off) = tf32(a - h);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+               " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+               :: "r"(d_tmem), "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+}
+
+// D = A_hi B_hi + A_hi B_lo + A_lo B_hi over K = 64 (8 steps of K = 8).
+__device__ __forceinline__ void issue_gemm(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                           uint32_t b_lo, uint32_t mbar) {
+  uint32_t acc = 0;
+  for (int kk = 0; kk < 8; ++kk) {
+    const uint32_t ko = uint32_t(kk) * 2 * kLbo;
+    mma_tf32(d_tmem, sdesc(a_hi + ko, kSboA), sdesc(b_hi + ko, kSboB), acc);
+    acc = 1;
+    mma_tf32(d_tmem, sdesc(a_hi + ko, kSboA), sdesc(b_lo + ko, kSboB), 1);
+    mma_tf32(d_tmem, sdesc(a_lo + ko, kSboA), sdesc(b_hi + ko, kSboB), 1);
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar));
+}
+
+// Bounded wait for the given phase parity; false when the limit ran out.
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(mbar), "r"(parity));
+    if (done) return true;
+  }
+  return false;
+}
+
+// 64 FP32 accumulator columns of TMEM lane (32 w + lane) from column col.
+__device__ __forceinline__ void tmem_row64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[32];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr + uint32_t(32 * h)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[32 * h + j] = __uint_as_float(r[j]);
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads) tc_kernel(float2* __restrict__ st, const __grid_constant__ TcDesc d) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* a_hi = sm;
+  unsigned char* a_lo = sm + kABytes;
+  unsigned char* b_hi = sm + 2 * kABytes;
+  unsigned char* b_lo = b_hi + kBBytes;
+  __shared__ uint32_t tmem_base;
+  __shared__ __align__(8) uint64_t mbar;
+  const int t = threadIdx.x;
+  // B = [[Re L^T, Im L^T], [-Im L^T, Re L^T]] (64 x 64), element (k, n) on row n of the K-major operand
+  for (int i = t; i < 64 * 64; i += kTcThreads) {
+    const int k = i >> 6, n = i & 63;
+    const float2 l = d.u[(n & 31) * 32 + (k & 31)];   // L^T[k][n] = L[n][k]
+    const float v = (k < 32) == (n < 32) ? l.x : (k < 32 ? l.y : -l.y);
+    put_split(b_hi, b_lo, koff(n, k, kSboB), v);
+  }
+  const uint32_t mb = saddr(&mbar);
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (t < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" :: "r"(saddr(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t d1 = tmem_base, d2 = tmem_base + 64;
+  const uint32_t lane = uint32_t(32 * (t >> 5)) << 16;   // this warp's TMEM lane quarter
+  const uint32_t ah = saddr(a_hi), al = saddr(a_lo), bh = saddr(b_hi), bl = saddr(b_lo);
+  const int tt = t >> 5, c = t & 31;                    // row t of D: tile tt, column / row c
+  uint32_t parity = 0;
+  bool ok = true;
+  const int64_t nitems = (d.ntiles + 3) / 4;
+  for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+    const int64_t tile0 = item * 4;
+    // A = T^T: element (k, c) of tile q goes to row 32 q + c, K index k (re) and 32 + k (im)
+    for (int i = t; i < 4 * 512; i += kTcThreads) {
+      const int q = i >> 9, w = i & 511;
+      const int k = w >> 4, cc = (w & 15) * 2;
+      float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (tile0 + q < d.ntiles) v = __ldcs(reinterpret_cast<const float4*>(st + ((tile0 + q) << 10)) + w);
+      put_split(a_hi, a_lo, koff(32 * q + cc, k, kSboA), v.x);
+      put_split(a_hi, a_lo, koff(32 * q + cc, 32 + k, kSboA), v.y);
+      put_split(a_hi, a_lo, koff(32 * q + cc + 1, k, kSboA), v.z);
+      put_split(a_hi, a_lo, koff(32 * q + cc + 1, 32 + k, kSboA), v.w);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (t == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      issue_gemm(d1, ah, al, bh, bl, mb);
+    }
+    ok = __syncthreads_and(wait_phase(mb, parity));
+    parity ^= 1;
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    float v[64];
+    tmem_row64(d1 + lane, v);   // v[n] = Re Y[n][c], v[32 + n] = Im Y[n][c] (tile tt)
+    // A = conj(Y): row 32 tt + n, K index c (re) and 32 + c (-im)
+#pragma unroll
+    for (int n = 0; n < 32; ++n) {
+      put_split(a_hi, a_lo, koff(32 * tt + n, c, kSboA), v[n]);
+      put_split(a_hi, a_lo, koff(32 * tt + n, 32 + c, kSboA), -v[32 + n]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (t == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      issue_gemm(d2, ah, al, bh, bl, mb);
+    }
+    ok = __syncthreads_and(wait_phase(mb, parity));
+    parity ^= 1;
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    tmem_row64(d2 + lane, v);   // conj(T') row c of tile tt
+    if (tile0 + tt < d.ntiles) {
+      float4* row = reinterpret_cast<float4*>(st + ((tile0 + tt) << 10) + (c << 5));
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        __stcs(row + j, make_float4(v[2 * j], -v[32 + 2 * j], v[2 * j + 1], -v[33 + 2 * j]));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  if (!ok) {
+    if (t == 0) atomicExch(d.err, 1);
+    (void)wait_phase(mb, parity ^ 1);   // bounded: let an MMA still in flight finish before TMEM is freed
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (t < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" :: "r"(tmem_base));
+}
+
+}  // namespace
+
+cudaError_t launch_tc(void* state, const TcDesc& d, cudaStream_t s) {
+  if (d.ntiles <= 0) return cudaSuccess;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes));
+  if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_kernel, kTcThreads, kSmemBytes);
+  if (err != cudaSuccess) return err;
+  const int64_t nitems = (d.ntiles + 3) / 4;
+  const int grid = int(std::min<int64_t>(nitems, int64_t(std::max(per_sm, 1)) * sms));
+  tc_kernel<<<grid, kTcThreads, kSmemBytes, s>>>(reinterpret_cast<float2*>(state), d);
+  return cudaGetLastError();
+}
+
+}  // namespace orkan

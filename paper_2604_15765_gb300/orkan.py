@@ -72,6 +72,7 @@ _SIGS = {
     "orkan_free": (C.c_int, [_h]),
     "orkan_set_stream": (C.c_int, [_h, C.c_void_p]),
     "orkan_set_fusion": (C.c_int, [_h, C.c_int, C.c_int]),
+    "orkan_set_tensor": (C.c_int, [_h, C.c_int]),
     "orkan_get_info": (C.c_int, [_h, _pi, _pi, _pi, _pi]),
     "orkan_autotune": (C.c_int, [C.c_int, C.c_int, _pi, _pi]),
     "orkan_device_ptr": (C.c_void_p, [_h]),
@@ -237,6 +238,10 @@ def orkan_init_observable(h, paulis, coeffs):
     s = "".join(paulis).encode()
     c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
     _check(_lib.orkan_init_observable(h, len(paulis), s, _dptr(c)), "orkan_init_observable")
+
+
+def orkan_set_tensor(h, mode: int):
+    _check(_lib.orkan_set_tensor(h, mode), "orkan_set_tensor")
 
 
 def orkan_set_picture(h, picture: int):

@@ -1,0 +1,122 @@
+"""Tensor-core passes (orkan_set_tensor): runs of in-tile single-Kraus ops
+composed into one 32 x 32 block and applied as L T L^dagger to every stored
+tile with tcgen05 MMAs (complex64, m = 5), against the oracle and against the
+CUDA-core passes of the same circuit.
+
+Covers: one- and two-qubit Haar unitaries, monomial gates and a one-operator
+Kraus map inside the tile; both pictures; a run longer than a fused pass
+(one launch for 40 ops); a run ended by a cross-tile op; a padded operator
+(n < m); a partial last work item (the stored tile count is not a multiple
+of four); and graph capture of the pass.
+"""
+import numpy as np
+import pytest
+
+from oracle import dense as D
+from workloads import synth as S
+
+pytestmark = pytest.mark.gpu
+
+ok = pytest.importorskip("paper_2604_15765_gb300.orkan")
+from paper_2604_15765_gb300 import circuit  # noqa: E402
+
+TOL = 1e-5
+
+
+def _intile(rng, n, count):
+    lo = min(n, 5)
+    ops = []
+    for i in range(count):
+        c = i % 5
+        if c in (0, 3) or lo == 1:
+            ops.append(S.op_unitary(S.haar_unitary(rng, 2), [int(rng.integers(lo))]))
+        elif c == 1:
+            a, b = rng.choice(lo, size=2, replace=False)
+            ops.append(S.op_unitary(S.haar_unitary(rng, 4), [int(a), int(b)]))
+        elif c == 2:
+            a, b = rng.choice(lo, size=2, replace=False)
+            ops.append(S.op_unitary(np.eye(4, dtype=np.complex128)[[0, 1, 3, 2]], [int(a), int(b)]))   # CNOT
+        else:
+            a, b = rng.choice(lo, size=2, replace=False)
+            K = np.sqrt(0.9) * S.haar_unitary(rng, 4)                                            # one Kraus operator
+            ops.append(S.op_kraus([K], [int(a), int(b)]))
+    return ops
+
+
+def _run(n, ops, mode, picture="schrodinger", H0=None, seed=0):
+    h = ok.orkan_alloc(n, ok.ORKAN_C64, 5)
+    try:
+        ok.orkan_set_tensor(h, mode)
+        if picture == "schrodinger":
+            ok.orkan_init_state(h, ok.ORKAN_INIT_DENSE, H0)
+        else:
+            ok.orkan_init_state(h, ok.ORKAN_INIT_DENSE, H0)
+            ok.orkan_set_picture(h, ok.ORKAN_OBSERVABLE)
+        p0 = ok.orkan_stats(h)["passes"]
+        circuit.run_circuit(h, ops, picture)
+        ok.orkan_sync(h)
+        return ok.orkan_to_dense(h), ok.orkan_stats(h)["passes"] - p0
+    finally:
+        ok.orkan_free(h)
+
+
+@pytest.mark.parametrize("n", [3, 5, 7, 8, 10])
+@pytest.mark.parametrize("picture", ["schrodinger", "heisenberg"])
+def test_tensor_pass_matches_oracle_and_cuda_cores(n, picture):
+    rng = S.rng_for(6000 + 10 * n + (picture == "heisenberg"))
+    H0 = S.ginibre_state(rng, 1 << n) if picture == "schrodinger" else S.random_hermitian(rng, 1 << n)
+    ops = _intile(rng, n, 12)
+    ref, _ = D.run_circuit(H0, ops, picture)
+    scale = max(1.0, float(np.max(np.abs(ref))))
+    tc, passes = _run(n, ops, 2, picture, H0)
+    cc, _ = _run(n, ops, 0, picture, H0)
+    assert passes == 1
+    assert np.max(np.abs(tc - ref)) <= TOL * scale
+    assert np.max(np.abs(tc - cc)) <= TOL * scale
+
+
+def test_long_run_is_one_tensor_pass_and_a_cross_tile_op_ends_it():
+    n = 9
+    rng = S.rng_for(6100)
+    rho = S.ginibre_state(rng, 1 << n)
+    ops = _intile(rng, n, 40) + [S.op_unitary(S.haar_unitary(rng, 4), [1, 8])] + _intile(rng, n, 7)
+    ref, _ = D.run_circuit(rho, ops)
+    got, passes = _run(n, ops, 1, "schrodinger", rho)
+    assert passes == 3          # 40 in-tile ops, the cross-tile op, 7 in-tile ops
+    assert np.max(np.abs(got - ref)) <= TOL
+
+
+def test_auto_mode_leaves_short_runs_on_cuda_cores():
+    n = 8
+    rng = S.rng_for(6200)
+    rho = S.ginibre_state(rng, 1 << n)
+    ops = [S.op_unitary(S.haar_unitary(rng, 2), [q]) for q in (0, 2, 4)]   # three single-qubit ops
+    a, _ = _run(n, ops, 1, "schrodinger", rho)
+    b, _ = _run(n, ops, 0, "schrodinger", rho)
+    assert np.array_equal(a, b)
+
+
+def test_captured_tensor_pass_replays():
+    n = 8
+    rng = S.rng_for(6300)
+    rho = S.ginibre_state(rng, 1 << n)
+    ops = _intile(rng, n, 10)
+    ref, _ = D.run_circuit(rho, ops + ops)
+    stream = __import__("torch").cuda.Stream()
+    h = ok.orkan_alloc(n, ok.ORKAN_C64, 5)
+    try:
+        ok.orkan_set_stream(h, stream.cuda_stream)
+        ok.orkan_set_tensor(h, 2)
+        ok.orkan_init_state(h, ok.ORKAN_INIT_DENSE, rho)
+        ok.orkan_capture_begin(h)
+        circuit.run_circuit(h, ops)
+        g = ok.orkan_capture_end(h)
+        try:
+            ok.orkan_graph_launch(h, g)
+            ok.orkan_graph_launch(h, g)
+        finally:
+            ok.orkan_graph_free(g)
+        ok.orkan_sync(h)
+        assert np.max(np.abs(ok.orkan_to_dense(h) - ref)) <= TOL
+    finally:
+        ok.orkan_free(h)
