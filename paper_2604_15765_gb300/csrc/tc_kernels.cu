@@ -159,18 +159,33 @@ __global__ void __launch_bounds__(kTcThreads) tc_kernel(float2* __restrict__ st,
   uint32_t parity = 0;
   bool ok = true;
   const int64_t nitems = (d.ntiles + 3) / 4;
+  const int warp = t >> 5, ln = t & 31;
+  // Load mapping (bank-light A stores): per step j, tile q, row k and 16-byte
+  // column pair cp of the 4 tiles come from (j, warp, lane):
+  //   lane = (k & 7) << 2 | (cp & 3), (j, warp) = q, k >> 3, cp >> 2.
+  float4 pre[16];
+  auto load_item = [&](int64_t it) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int h6 = j * 4 + warp;
+      const int q = h6 >> 4, k = ((h6 >> 2) & 3) * 8 + (ln >> 2), cp = (h6 & 3) * 4 + (ln & 3);
+      const int64_t tile = it * 4 + q;
+      pre[j] = tile < d.ntiles ? __ldcs(reinterpret_cast<const float4*>(st + (tile << 10)) + (k * 16 + cp))
+                               : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+  };
+  if (int64_t(blockIdx.x) < nitems) load_item(blockIdx.x);
   for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
     const int64_t tile0 = item * 4;
     // A = T^T: element (k, c) of tile q goes to row 32 q + c, K index k (re) and 32 + k (im)
-    for (int i = t; i < 4 * 512; i += kTcThreads) {
-      const int q = i >> 9, w = i & 511;
-      const int k = w >> 4, cc = (w & 15) * 2;
-      float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      if (tile0 + q < d.ntiles) v = __ldcs(reinterpret_cast<const float4*>(st + ((tile0 + q) << 10)) + w);
-      put_split(a_hi, a_lo, koff(32 * q + cc, k, kSboA), v.x);
-      put_split(a_hi, a_lo, koff(32 * q + cc, 32 + k, kSboA), v.y);
-      put_split(a_hi, a_lo, koff(32 * q + cc + 1, k, kSboA), v.z);
-      put_split(a_hi, a_lo, koff(32 * q + cc + 1, 32 + k, kSboA), v.w);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int h6 = j * 4 + warp;
+      const int q = h6 >> 4, k = ((h6 >> 2) & 3) * 8 + (ln >> 2), cc = ((h6 & 3) * 4 + (ln & 3)) * 2;
+      put_split(a_hi, a_lo, koff(32 * q + cc, k, kSboA), pre[j].x);
+      put_split(a_hi, a_lo, koff(32 * q + cc, 32 + k, kSboA), pre[j].y);
+      put_split(a_hi, a_lo, koff(32 * q + cc + 1, k, kSboA), pre[j].z);
+      put_split(a_hi, a_lo, koff(32 * q + cc + 1, 32 + k, kSboA), pre[j].w);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
@@ -178,17 +193,38 @@ __global__ void __launch_bounds__(kTcThreads) tc_kernel(float2* __restrict__ st,
       asm volatile("tcgen05.fence::after_thread_sync;");
       issue_gemm(d1, ah, al, bh, bl, mb);
     }
+    // the next item's tiles stream in while the tensor cores work
+    if (item + gridDim.x < nitems) load_item(item + gridDim.x);
     ok = __syncthreads_and(wait_phase(mb, parity));
     parity ^= 1;
     if (!ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
     float v[64];
     tmem_row64(d1 + lane, v);   // v[n] = Re Y[n][c], v[32 + n] = Im Y[n][c] (tile tt)
-    // A = conj(Y): row 32 tt + n, K index c (re) and 32 + c (-im)
+    // A = conj(Y): row 32 tt + n, K index c (re) and 32 + c (-im).  Step s writes
+    // n = (s + g) & 31, g = c >> 2, so that a warp's 32 stores hit 32 banks.
+    const int g = c >> 2;
 #pragma unroll
-    for (int n = 0; n < 32; ++n) {
-      put_split(a_hi, a_lo, koff(32 * tt + n, c, kSboA), v[n]);
-      put_split(a_hi, a_lo, koff(32 * tt + n, 32 + c, kSboA), -v[32 + n]);
+    for (int s = 0; s < 32; ++s) {
+      float re[8], im[8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        re[x] = v[(s + x) & 31];
+        im[x] = v[32 + ((s + x) & 31)];
+      }
+#pragma unroll
+      for (int lvl = 0; lvl < 3; ++lvl) {
+        const bool bit = (g >> lvl) & 1;
+        const int span = 1 << lvl;
+#pragma unroll
+        for (int x = 0; x < 8; x += 2 * span) {
+          re[x] = bit ? re[x + span] : re[x];
+          im[x] = bit ? im[x + span] : im[x];
+        }
+      }
+      const int n = (s + g) & 31;
+      put_split(a_hi, a_lo, koff(32 * tt + n, c, kSboA), re[0]);
+      put_split(a_hi, a_lo, koff(32 * tt + n, 32 + c, kSboA), -im[0]);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
