@@ -386,6 +386,44 @@ def _request_errors(reqs, res, ref):
     return out
 
 
+def tensor_study(ok, circuit, n, m, stream, reps=5):
+    """complex64 in-tile runs of 1, 2, 4 and 8 Haar two-qubit unitaries on the
+    tile's qubits: the CUDA-core fused pass (orkan_set_tensor 0) against the
+    tensor-core pass of the composed block (mode 2); time per run and the
+    passes' HBM rate (2 x stored bytes / pass time)."""
+    from workloads import synth as S
+    rng = S.rng_for(S.BASE_SEED + 15)
+    psi = S.haar_state_vector(rng, 1 << n)
+    nb = 2 * ok.orkan_bytes(n, ok.ORKAN_C64, m)
+    out = {"n": n, "dtype": "c64", "tile_log2": m}
+    for count in (1, 2, 4, 8):
+        ops = []
+        for _ in range(count):
+            a, b = rng.choice(m, size=2, replace=False)
+            ops.append(S.op_unitary(S.haar_unitary(rng, 4), [int(a), int(b)]))
+        row = {}
+        for label, mode in (("cuda_cores", 0), ("tensor_cores", 2)):
+            h = ok.orkan_alloc(n, ok.ORKAN_C64, m)
+            ok.orkan_set_stream(h, stream)
+            ok.orkan_set_fusion(h, 16, True)
+            ok.orkan_set_tensor(h, mode)
+            ok.orkan_init_state(h, ok.ORKAN_INIT_PURE, psi)
+            circuit.run_circuit(h, ops)
+            ok.orkan_sync(h)
+            ok.orkan_set_timing(h, True)
+            ok.orkan_pass_time(h)
+            for _ in range(reps):
+                circuit.run_circuit(h, ops)
+                ok.orkan_flush(h)
+            ms, cnt = ok.orkan_pass_time(h)
+            ok.orkan_free(h)
+            row[label] = {"ms_per_run": round(ms / reps, 4), "passes_per_run": cnt / reps,
+                          "pass_GBps": round(nb / (ms / cnt * 1e-3) / 1e9, 1)}
+        row["speedup"] = round(row["cuda_cores"]["ms_per_run"] / row["tensor_cores"]["ms_per_run"], 2)
+        out[f"u2_x{count}"] = row
+    return out
+
+
 def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=True, batch_max_n=9):
     """Continuous batching vs one-at-a-time plain FP64 on the same requests.
     The plain arm runs every request alone, one pass per op, in native FP64
@@ -1064,6 +1102,7 @@ def main(argv=None):
     serving_res = None
     if not args.no_variants and world == 1:
         per_op = per_op_table(ok, wl, n, m, ("df64", "c128", "c64"), stream, torch)
+        per_op["tensor_core_c64"] = tensor_study(ok, circuit, n, m, stream)
         from workloads import synth as S
         serving_res = serving_study(S.serving_stream(count=args.serve_requests), torch, budget=32 << 30)
         serving_res["small_requests"] = small_request_study(S, torch)

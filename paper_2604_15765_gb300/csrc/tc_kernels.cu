@@ -260,15 +260,16 @@ __global__ void __launch_bounds__(kTcThreads) tc_kernel(float2* __restrict__ st,
 
 cudaError_t launch_tc(void* state, const TcDesc& d, cudaStream_t s) {
   if (d.ntiles <= 0) return cudaSuccess;
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes));
-  if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_kernel, kTcThreads, kSmemBytes);
   if (err != cudaSuccess) return err;
+  // two CTAs per SM (96 KiB of shared memory and 128 x 255 registers each), so
+  // that one CTA's tile loads and operand stores overlap the other's MMAs
   const int64_t nitems = (d.ntiles + 3) / 4;
-  const int grid = int(std::min<int64_t>(nitems, int64_t(std::max(per_sm, 1)) * sms));
+  const int grid = int(std::min<int64_t>(nitems, int64_t(2) * sms));
   tc_kernel<<<grid, kTcThreads, kSmemBytes, s>>>(reinterpret_cast<float2*>(state), d);
   return cudaGetLastError();
 }
