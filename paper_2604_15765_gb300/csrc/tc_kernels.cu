@@ -21,8 +21,8 @@
 //
 // tcgen05.mma (kind::tf32, cta_group::1, M = 128, N = 64, K = 8 per
 // instruction) is issued by one thread; operands are K-major, no swizzle,
-// 8-row x 16-byte core matrices (leading byte offset 128 B along K, stride
-// byte offset 2048 B between 8-row groups); the FP32 accumulators live in
+// 8-row x 16-byte core matrices (leading byte offset 144 B along K, stride
+// byte offset 2304 B between 8-row groups); the FP32 accumulators live in
 // TMEM (128 lanes x 64 columns per GEMM) and come back with tcgen05.ld
 // 32x32b (thread t holds row t).  Completion is signalled by tcgen05.commit
 // on an mbarrier; every wait on it is bounded and sets an error word instead
@@ -39,12 +39,17 @@ namespace orkan {
 namespace {
 
 constexpr int kTcThreads = 128;
-constexpr uint32_t kLbo = 128;                 // K-direction core-matrix stride
-constexpr uint32_t kSboA = 2048;               // 8-row group stride (16 K cores x 128 B)
-constexpr uint32_t kSboB = 2048;
-constexpr uint32_t kABytes = 128 * 64 * 4;     // one A operand (hi or lo): 32 KiB
-constexpr uint32_t kBBytes = 64 * 64 * 4;      // one B operand: 16 KiB
-constexpr uint32_t kSmemBytes = 2 * kABytes + 2 * kBBytes;   // 96 KiB
+// K-direction core-matrix stride: 144 B instead of the packed 128 B leaves a
+// 16-byte gap after each core matrix, which puts the four 32-bit words of K
+// core c of row r in banks 4 (c + r) .. 4 (c + r) + 3 (mod 32): a warp storing
+// 32 consecutive K indices of one row, or rows 0..7 x 4 K indices, hits 32
+// distinct banks.
+constexpr uint32_t kLbo = 144;
+constexpr uint32_t kSboA = 16 * kLbo;          // 8-row group stride (16 K cores)
+constexpr uint32_t kSboB = 16 * kLbo;
+constexpr uint32_t kABytes = 16 * kSboA;       // one A operand (hi or lo), 128 rows: 36 KiB
+constexpr uint32_t kBBytes = 8 * kSboB;        // one B operand, 64 rows: 18 KiB
+constexpr uint32_t kSmemBytes = 2 * kABytes + 2 * kBBytes;   // 108 KiB
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(64 >> 3) << 17) | (uint32_t(128 >> 4) << 24);
 constexpr long long kWaitLimit = 1 << 24;      // polls of one mbarrier phase before giving up
 
@@ -70,7 +75,7 @@ __device__ __forceinline__ float tf32(float x) {
 __device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, uint32_t off, float a) {
   const float h = tf32(a);
   *reinterpret_cast<float*>(hi + off) = h;
-  *reinterpret_cast<float*>(lo + off) = tf32(a - h);
+  *reinterpret_cast<float*>(lo + off) = a - h;   // the MMA reads the TF32 part of the low word
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t acc) {
@@ -201,30 +206,12 @@ __global__ void __launch_bounds__(kTcThreads) tc_kernel(float2* __restrict__ st,
     asm volatile("tcgen05.fence::after_thread_sync;");
     float v[64];
     tmem_row64(d1 + lane, v);   // v[n] = Re Y[n][c], v[32 + n] = Im Y[n][c] (tile tt)
-    // A = conj(Y): row 32 tt + n, K index c (re) and 32 + c (-im).  Step s writes
-    // n = (s + g) & 31, g = c >> 2, so that a warp's 32 stores hit 32 banks.
-    const int g = c >> 2;
+    // A = conj(Y): row 32 tt + n, K index c (re) and 32 + c (-im); the
+    // 144-byte core stride spreads a warp's 32 K indices over 32 banks
 #pragma unroll
-    for (int s = 0; s < 32; ++s) {
-      float re[8], im[8];
-#pragma unroll
-      for (int x = 0; x < 8; ++x) {
-        re[x] = v[(s + x) & 31];
-        im[x] = v[32 + ((s + x) & 31)];
-      }
-#pragma unroll
-      for (int lvl = 0; lvl < 3; ++lvl) {
-        const bool bit = (g >> lvl) & 1;
-        const int span = 1 << lvl;
-#pragma unroll
-        for (int x = 0; x < 8; x += 2 * span) {
-          re[x] = bit ? re[x + span] : re[x];
-          im[x] = bit ? im[x + span] : im[x];
-        }
-      }
-      const int n = (s + g) & 31;
-      put_split(a_hi, a_lo, koff(32 * tt + n, c, kSboA), re[0]);
-      put_split(a_hi, a_lo, koff(32 * tt + n, 32 + c, kSboA), -im[0]);
+    for (int n = 0; n < 32; ++n) {
+      put_split(a_hi, a_lo, koff(32 * tt + n, c, kSboA), v[n]);
+      put_split(a_hi, a_lo, koff(32 * tt + n, 32 + c, kSboA), -v[32 + n]);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -266,7 +253,7 @@ cudaError_t launch_tc(void* state, const TcDesc& d, cudaStream_t s) {
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes));
   if (err != cudaSuccess) return err;
-  // two CTAs per SM (96 KiB of shared memory and 128 x 255 registers each), so
+  // two CTAs per SM (108 KiB of shared memory and 128 x 255 registers each), so
   // that one CTA's tile loads and operand stores overlap the other's MMAs
   const int64_t nitems = (d.ntiles + 3) / 4;
   const int grid = int(std::min<int64_t>(nitems, int64_t(2) * sms));
