@@ -424,7 +424,7 @@ def tensor_study(ok, circuit, n, m, stream, reps=5):
     return out
 
 
-def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=True, batch_max_n=9):
+def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=True, batch_max_n=8):
     """Continuous batching vs one-at-a-time plain FP64 on the same requests.
     The plain arm runs every request alone, one pass per op, in native FP64
     (c64 requests too); its results are the reference for every served arm's
@@ -507,16 +507,16 @@ def _run_timed(ok, circuit, torch, stream, n, dt, m, fusion, compose, ops, pauli
 def small_request_study(S, torch, count=600, budget=8 << 30):
     """Requests of n = 4..10 (the serving mix's small end, where every op is
     launch-bound): solves/s with the slots alone, and with the batched
-    persistent launch for n <= 9 beside them; same requests, own dtypes."""
+    persistent launch for n <= 8 beside them; same requests, own dtypes."""
     from paper_2604_15765_gb300 import serving
     reqs = S.serving_stream(count=count, seed=S.BASE_SEED + 14, n_range=(4, 10))
     out = {"requests": count, "n_range": [4, 10]}
     res = {}
-    for label, bmax in (("slots_only", None), ("batched_n_le_9", 9)):
+    for label, bmax in (("slots_only", None), ("batched_n_le_8", 8)):
         res[label], st = serving.serve(reqs, budget, slots=8, realtime=False, batch_max_n=bmax)
         out[label] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
-    out.update({"batched_" + k: v for k, v in _request_errors(reqs, res["batched_n_le_9"], res["slots_only"]).items()})
-    out["speedup_solves_per_s"] = round(out["batched_n_le_9"]["solves_per_s"] / out["slots_only"]["solves_per_s"], 2)
+    out.update({"batched_" + k: v for k, v in _request_errors(reqs, res["batched_n_le_8"], res["slots_only"]).items()})
+    out["speedup_solves_per_s"] = round(out["batched_n_le_8"]["solves_per_s"] / out["slots_only"]["solves_per_s"], 2)
     torch.cuda.synchronize()
     return out
 
@@ -976,7 +976,7 @@ def main(argv=None):
             # request-level replicas: each rank serves its routed share on its own GPU, nothing is
             # exchanged while requests run; results and latencies are gathered once at the end
             from paper_2604_15765_gb300 import serving
-            _, cap = serving.serve_replicated(reqs, 64 << 30, slots=8, realtime=False, batch_max_n=9)
+            _, cap = serving.serve_replicated(reqs, 64 << 30, slots=8, realtime=False, batch_max_n=8)
             st = {"replicated_capacity": cap}
         else:
             st = serving_study(reqs, torch, budget=64 << 30, realtime_fracs=(0.5, 0.9, 1.2))

@@ -5,6 +5,8 @@ meaning; the library plans, fuses and runs the passes on the GPU.
 """
 from __future__ import annotations
 
+import numpy as np
+
 from . import orkan as ok
 
 
@@ -35,41 +37,75 @@ def apply_op(h, op, picture: str = "schrodinger"):
     return None
 
 
+# orkan_op as a NumPy record (the ctypes structure's field offsets), so that an
+# op list is marshalled with list appends and one record-array fill instead of
+# per-field ctypes attribute writes
+_OP_DTYPE = np.dtype({"names": ["kind", "k", "q0", "q1", "q2", "r", "outcome", "param", "mats"],
+                      "formats": ["<i4", "<i4", "<i4", "<i4", "<i4", "<i4", "<i4", "<f8", "<u8"],
+                      "offsets": [0, 4, 8, 12, 16, 20, 24, 32, 40], "itemsize": 48})
+_KIND = {"unitary": ok.ORKAN_OP_UNITARY, "kraus": ok.ORKAN_OP_KRAUS, "depolarize": ok.ORKAN_OP_DEPOLARIZE,
+         "dephase": ok.ORKAN_OP_DEPHASE, "ampdamp": ok.ORKAN_OP_AMPDAMP}
+
+
 def marshal(ops, picture: str = "schrodinger"):
-    """Op dicts -> (OrkanOp array, kept-alive matrices, number of MEASURE ops).
+    """Op dicts -> (OrkanOp array, kept-alive buffers, number of MEASURE ops).
     On an observable a measurement becomes the projection b = (u >= 0.5)."""
-    import numpy as np
-    arr = (ok.OrkanOp * len(ops))()
-    keep = []
+    n = len(ops)
+    kind, k, qs, r, outc, param, moff = [], [], [], [], [], [], []
+    mats = []
+    off = 0
     nmeas = 0
-    for o, op in zip(arr, ops):
-        kind = op["kind"]
+    for op in ops:
+        kd = op["kind"]
         q = op["qubits"]
-        o.k = len(q)
-        for l in range(3):
-            o.qubits[l] = q[l] if len(q) > l else 0
-        if kind in ("unitary", "kraus"):
-            mats = np.ascontiguousarray(np.asarray(op["matrix"] if kind == "unitary" else op["mats"], np.complex128))
-            keep.append(mats)
-            o.kind = ok.ORKAN_OP_UNITARY if kind == "unitary" else ok.ORKAN_OP_KRAUS
-            o.r = 1 if kind == "unitary" else mats.shape[0]
-            o.mats = mats.view(np.float64).ctypes.data_as(ok._pd)
-        elif kind == "depolarize":
-            o.kind, o.param = ok.ORKAN_OP_DEPOLARIZE, op["p"]
-        elif kind == "dephase":
-            o.kind, o.param = ok.ORKAN_OP_DEPHASE, op["p"]
-        elif kind == "ampdamp":
-            o.kind, o.param = ok.ORKAN_OP_AMPDAMP, op["gamma"]
-        elif kind == "measure" and picture == "schrodinger":
-            o.kind, o.param = ok.ORKAN_OP_MEASURE, op["u"]
-            nmeas += 1
-        elif kind == "measure":
-            o.kind, o.outcome = ok.ORKAN_OP_PROJECT, 0 if op["u"] < 0.5 else 1
-        elif kind == "project":
-            o.kind, o.outcome = ok.ORKAN_OP_PROJECT, op["outcome"]
+        k.append(len(q))
+        qs.append((q + [0, 0, 0])[:3] if isinstance(q, list) else (list(q) + [0, 0, 0])[:3])
+        o = 0
+        pm = 0.0
+        if kd == "unitary" or kd == "kraus":
+            m = np.asarray(op["matrix"] if kd == "unitary" else op["mats"], np.complex128)
+            mats.append(m.reshape(-1))
+            r.append(1 if kd == "unitary" else m.shape[0])
+            moff.append(off)
+            off += m.size
+            kind.append(_KIND[kd])
         else:
-            raise ValueError(kind)
-    return arr, keep, nmeas
+            r.append(0)
+            moff.append(-1)
+            if kd in ("depolarize", "dephase"):
+                kind.append(_KIND[kd])
+                pm = op["p"]
+            elif kd == "ampdamp":
+                kind.append(_KIND[kd])
+                pm = op["gamma"]
+            elif kd == "measure" and picture == "schrodinger":
+                kind.append(ok.ORKAN_OP_MEASURE)
+                pm = op["u"]
+                nmeas += 1
+            elif kd == "measure":
+                kind.append(ok.ORKAN_OP_PROJECT)
+                o = 0 if op["u"] < 0.5 else 1
+            elif kd == "project":
+                kind.append(ok.ORKAN_OP_PROJECT)
+                o = op["outcome"]
+            else:
+                raise ValueError(kd)
+        outc.append(o)
+        param.append(pm)
+    rec = np.zeros(max(n, 1), dtype=_OP_DTYPE)
+    allm = np.ascontiguousarray(np.concatenate(mats)) if mats else np.zeros(1, np.complex128)
+    if n:
+        rec["kind"][:n] = kind
+        rec["k"][:n] = k
+        qa = np.asarray(qs, dtype=np.int32).reshape(n, 3)
+        rec["q0"][:n], rec["q1"][:n], rec["q2"][:n] = qa[:, 0], qa[:, 1], qa[:, 2]
+        rec["r"][:n] = r
+        rec["outcome"][:n] = outc
+        rec["param"][:n] = param
+        mo = np.asarray(moff, dtype=np.int64)
+        rec["mats"][:n] = np.where(mo >= 0, allm.ctypes.data + 16 * mo, 0).astype(np.uint64)
+    arr = (ok.OrkanOp * max(n, 1)).from_buffer(rec)
+    return arr, [rec, allm], nmeas
 
 
 def run_circuit(h, ops, picture: str = "schrodinger", native: bool = True):
