@@ -95,8 +95,35 @@ Mat pauli_string(int a, int k) {
   return P;
 }
 
+// k = 1 on fixed-size arrays (no heap traffic per product): every op of a
+// circuit goes through here once, so its host cost bounds small-operator rates.
+std::vector<double> ptm1(const std::vector<Mat>& kraus, bool adjoint) {
+  std::vector<double> R(16, 0.0);
+  for (int b = 0; b < 4; ++b) {
+    cd img[4] = {0.0, 0.0, 0.0, 0.0};   // Phi(P_b) (or Phi*(P_b)), row-major 2 x 2
+    for (const Mat& K : kraus) {
+      // M = adjoint ? K^dagger : K; img += M P_b M^dagger
+      cd M[4];
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) M[2 * i + j] = adjoint ? std::conj(K[2 * j + i]) : K[2 * i + j];
+      cd MP[4];
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) MP[2 * i + j] = M[2 * i] * kPauli[b][j] + M[2 * i + 1] * kPauli[b][2 + j];
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) img[2 * i + j] += MP[2 * i] * std::conj(M[2 * j]) + MP[2 * i + 1] * std::conj(M[2 * j + 1]);
+    }
+    for (int a = 0; a < 4; ++a) {
+      // tr(P_a img) / 2
+      const cd tr = kPauli[a][0] * img[0] + kPauli[a][1] * img[2] + kPauli[a][2] * img[1] + kPauli[a][3] * img[3];
+      R[4 * a + b] = 0.5 * tr.real();
+    }
+  }
+  return R;
+}
+
 // Pauli transfer matrix R[a][b] = 2^-k Re tr(P_a Phi(P_b)) of the Kraus set.
 std::vector<double> ptm(int k, const std::vector<Mat>& kraus, bool adjoint) {
+  if (k == 1) return ptm1(kraus, adjoint);
   const int d = 1 << k, np = 1 << (2 * k);
   std::vector<Mat> P(np);
   for (int a = 0; a < np; ++a) P[a] = pauli_string(a, k);
