@@ -52,6 +52,8 @@ constexpr uint32_t kBBytes = 8 * kSboB;        // one B operand, 64 rows: 18 KiB
 constexpr uint32_t kSmemBytes = 2 * kABytes + 2 * kBBytes;   // 108 KiB
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(64 >> 3) << 17) | (uint32_t(128 >> 4) << 24);
 constexpr long long kWaitLimit = 1 << 24;      // polls of one mbarrier phase before giving up
+constexpr uint32_t kOutRow = 272;              // padded byte stride of a staged output row
+static_assert(128 * kOutRow <= kABytes, "output staging fits the A_hi buffer");
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -225,14 +227,25 @@ __global__ void __launch_bounds__(kTcThreads) tc_kernel(float2* __restrict__ st,
     if (!ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
     tmem_row64(d2 + lane, v);   // conj(T') row c of tile tt
-    if (tile0 + tt < d.ntiles) {
-      float4* row = reinterpret_cast<float4*>(st + ((tile0 + tt) << 10) + (c << 5));
+    // stage the four output tiles in the (now free) A_hi buffer, rows padded
+    // to 272 bytes so a warp's 16-byte stores take four wavefronts, then
+    // write them to HBM with each warp covering 512 contiguous bytes per store
+    {
+      float4* orow = reinterpret_cast<float4*>(a_hi + t * kOutRow);
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        __stcs(row + j, make_float4(v[2 * j], -v[32 + 2 * j], v[2 * j + 1], -v[33 + 2 * j]));
+      for (int j = 0; j < 16; ++j) orow[j] = make_float4(v[2 * j], -v[32 + 2 * j], v[2 * j + 1], -v[33 + 2 * j]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int f = j * kTcThreads + t;       // float4 index in the item: tile q, row r, column pair cq
+      const int q = f >> 9, r = (f >> 4) & 31, cq = f & 15;
+      if (tile0 + q < d.ntiles)
+        __stcs(reinterpret_cast<float4*>(st + ((tile0 + q) << 10)) + (f & 511),
+               *reinterpret_cast<const float4*>(a_hi + (32 * q + r) * kOutRow + 16 * cq));
+    }
+    __syncthreads();   // the staged rows are read before the next item's operands overwrite them
   }
   if (!ok) {
     if (t == 0) atomicExch(d.err, 1);
