@@ -63,7 +63,8 @@ def parse_args(argv=None):
     p.add_argument("--no-variants", action="store_true", help="skip the c128 / c64 / unfused comparison runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=20.0)
-    p.add_argument("--workload", choices=["sweep", "serving", "brickwork", "precision", "paper", "relabel", "pipes"],
+    p.add_argument("--workload", choices=["sweep", "serving", "brickwork", "precision", "paper", "relabel", "pipes",
+                                          "tensor", "batch"],
                    default="sweep")
     p.add_argument("--depth", type=int, default=40)
     p.add_argument("--bw-depth", type=int, default=6,
@@ -969,6 +970,29 @@ def main(argv=None):
                 "data": "synthetic", "config": cfg}
         line.update(extra)
         print(json.dumps(line), flush=True)
+        return 0
+    if args.workload == "tensor":
+        # complex64 in-tile runs: CUDA-core fused pass vs the tensor-core pass of the composed block
+        ts = tensor_study(ok, circuit, args.n, m, stream, reps=args.steps)
+        print(json.dumps({"workload": "tensor", "metric": "in-tile run time and pass GB/s", "tensor_core_c64": ts}),
+              flush=True)
+        return 0
+    if args.workload == "batch":
+        # the batched persistent launch on 300 served requests of n = 4..8 at one dtype, one launch
+        from paper_2604_15765_gb300 import serving
+        from workloads import synth as S
+        dt = args.dtype if args.dtype in ("c128", "c64") else "c128"
+        reqs = serving.prepare([dict(r, dtype=dt) for r in
+                                S.serving_stream(count=300, seed=S.BASE_SEED + 16, n_range=(4, 8))])
+        pool = serving.HandlePool(8 << 30)
+        serving.run_batched(pool, reqs[:8])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        serving.run_batched(pool, reqs)
+        dt_s = time.perf_counter() - t0
+        pool.close()
+        print(json.dumps({"workload": "batch", "dtype": dt, "requests": len(reqs), "solves_per_s": len(reqs) / dt_s,
+                          "ops_per_s": sum(len(r["ops"]) for r in reqs) / dt_s}), flush=True)
         return 0
     if args.workload == "serving":
         from workloads import synth as S
