@@ -24,7 +24,8 @@
 // 8-row x 16-byte core matrices (leading byte offset 144 B along K, stride
 // byte offset 2304 B between 8-row groups); the FP32 accumulators live in
 // TMEM (128 lanes x 64 columns per GEMM) and come back with tcgen05.ld
-// 32x32b (thread t holds row t).  Completion is signalled by tcgen05.commit
+// 32x32b: 256 threads, thread t reads lane t mod 128 (its warp's lane quarter
+// is warp mod 4) and the half t / 128 of the row's index range.  Completion is signalled by tcgen05.commit
 // on an mbarrier; every wait on it is bounded and sets an error word instead
 // of hanging.  complex64 storage (8-byte elements) at m = 5.
 #include <algorithm>
@@ -38,7 +39,7 @@
 namespace orkan {
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;   // two warpgroups: TMEM lane quarter = warp % 4, the halves split the columns
 // K-direction core-matrix stride: 144 B instead of the packed 128 B leaves a
 // 16-byte gap after each core matrix, which puts the four 32-bit words of K
 // core c of row r in banks 4 (c + r) .. 4 (c + r) + 3 (mod 32): a warp storing
@@ -111,26 +112,19 @@ __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-// 64 FP32 accumulator columns of TMEM lane (32 w + lane) from column col.
-__device__ __forceinline__ void tmem_row64(uint32_t taddr, float (&v)[64]) {
-  uint32_t r[32];
+// 16 FP32 accumulator columns of this thread's TMEM lane, from column address taddr.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                 : "r"(taddr + uint32_t(32 * h)));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[32 * h + j] = __uint_as_float(r[j]);
-  }
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__global__ void __launch_bounds__(kTcThreads) tc_kernel(float2* __restrict__ st, const __grid_constant__ TcDesc d) {
+__global__ void __launch_bounds__(kTcThreads, 2) tc_kernel(float2* __restrict__ st, const __grid_constant__ TcDesc d) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* a_hi = sm;
   unsigned char* a_lo = sm + kABytes;
@@ -160,21 +154,23 @@ __global__ void __launch_bounds__(kTcThreads) tc_kernel(float2* __restrict__ st,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t d1 = tmem_base, d2 = tmem_base + 64;
-  const uint32_t lane = uint32_t(32 * (t >> 5)) << 16;   // this warp's TMEM lane quarter
+  const int warp = t >> 5, ln = t & 31;
+  const uint32_t lane = uint32_t(32 * (warp & 3)) << 16;   // this warp's TMEM lane quarter
   const uint32_t ah = saddr(a_hi), al = saddr(a_lo), bh = saddr(b_hi), bl = saddr(b_lo);
-  const int tt = t >> 5, c = t & 31;                    // row t of D: tile tt, column / row c
+  const int row = t & 127, half = t >> 7;               // accumulator row (tile tt, column / row c) and half
+  const int tt = row >> 5, c = row & 31;
+  const int n0 = 16 * half;                             // this thread's 16 of the 32 row / column indices n
   uint32_t parity = 0;
   bool ok = true;
   const int64_t nitems = (d.ntiles + 3) / 4;
-  const int warp = t >> 5, ln = t & 31;
-  // Load mapping (bank-light A stores): per step j, tile q, row k and 16-byte
+  // Load mapping (conflict-free A stores): per step j, tile q, row k and 16-byte
   // column pair cp of the 4 tiles come from (j, warp, lane):
   //   lane = (k & 7) << 2 | (cp & 3), (j, warp) = q, k >> 3, cp >> 2.
-  float4 pre[16];
+  float4 pre[8];
   auto load_item = [&](int64_t it) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int h6 = j * 4 + warp;
+    for (int j = 0; j < 8; ++j) {
+      const int h6 = j * 8 + warp;
       const int q = h6 >> 4, k = ((h6 >> 2) & 3) * 8 + (ln >> 2), cp = (h6 & 3) * 4 + (ln & 3);
       const int64_t tile = it * 4 + q;
       pre[j] = tile < d.ntiles ? __ldcs(reinterpret_cast<const float4*>(st + (tile << 10)) + (k * 16 + cp))
@@ -186,8 +182,8 @@ __global__ void __launch_bounds__(kTcThreads) tc_kernel(float2* __restrict__ st,
     const int64_t tile0 = item * 4;
     // A = T^T: element (k, c) of tile q goes to row 32 q + c, K index k (re) and 32 + k (im)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int h6 = j * 4 + warp;
+    for (int j = 0; j < 8; ++j) {
+      const int h6 = j * 8 + warp;
       const int q = h6 >> 4, k = ((h6 >> 2) & 3) * 8 + (ln >> 2), cc = ((h6 & 3) * 4 + (ln & 3)) * 2;
       put_split(a_hi, a_lo, koff(32 * q + cc, k, kSboA), pre[j].x);
       put_split(a_hi, a_lo, koff(32 * q + cc, 32 + k, kSboA), pre[j].y);
@@ -206,14 +202,15 @@ __global__ void __launch_bounds__(kTcThreads) tc_kernel(float2* __restrict__ st,
     parity ^= 1;
     if (!ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    float v[64];
-    tmem_row64(d1 + lane, v);   // v[n] = Re Y[n][c], v[32 + n] = Im Y[n][c] (tile tt)
-    // A = conj(Y): row 32 tt + n, K index c (re) and 32 + c (-im); the
-    // 144-byte core stride spreads a warp's 32 K indices over 32 banks
+    float vr[16], vi[16];
+    tmem_ld16(d1 + lane + uint32_t(n0), vr);        // Re Y[n][c], n = n0 .. n0 + 15 (tile tt)
+    tmem_ld16(d1 + lane + uint32_t(32 + n0), vi);   // Im Y[n][c]
+    // A = conj(Y): row 32 tt + n, K index c (re) and 32 + c (-im); with the
+    // 144-byte core stride a warp's 32 K indices land in 32 banks
 #pragma unroll
-    for (int n = 0; n < 32; ++n) {
-      put_split(a_hi, a_lo, koff(32 * tt + n, c, kSboA), v[n]);
-      put_split(a_hi, a_lo, koff(32 * tt + n, 32 + c, kSboA), -v[32 + n]);
+    for (int j = 0; j < 16; ++j) {
+      put_split(a_hi, a_lo, koff(32 * tt + n0 + j, c, kSboA), vr[j]);
+      put_split(a_hi, a_lo, koff(32 * tt + n0 + j, 32 + c, kSboA), -vi[j]);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -226,19 +223,20 @@ __global__ void __launch_bounds__(kTcThreads) tc_kernel(float2* __restrict__ st,
     parity ^= 1;
     if (!ok) break;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    tmem_row64(d2 + lane, v);   // conj(T') row c of tile tt
+    tmem_ld16(d2 + lane + uint32_t(n0), vr);        // Re conj(T')[c][n] = Re T'[c][n]
+    tmem_ld16(d2 + lane + uint32_t(32 + n0), vi);   // Im conj(T')[c][n] = -Im T'[c][n]
     // stage the four output tiles in the (now free) A_hi buffer, rows padded
     // to 272 bytes so a warp's 16-byte stores take four wavefronts, then
     // write them to HBM with each warp covering 512 contiguous bytes per store
     {
-      float4* orow = reinterpret_cast<float4*>(a_hi + t * kOutRow);
+      float4* orow = reinterpret_cast<float4*>(a_hi + row * kOutRow + 8 * n0);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) orow[j] = make_float4(v[2 * j], -v[32 + 2 * j], v[2 * j + 1], -v[33 + 2 * j]);
+      for (int j = 0; j < 8; ++j) orow[j] = make_float4(vr[2 * j], -vi[2 * j], vr[2 * j + 1], -vi[2 * j + 1]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < 8; ++j) {
       const int f = j * kTcThreads + t;       // float4 index in the item: tile q, row r, column pair cq
       const int q = f >> 9, r = (f >> 4) & 31, cq = f & 15;
       if (tile0 + q < d.ntiles)
@@ -266,7 +264,7 @@ cudaError_t launch_tc(void* state, const TcDesc& d, cudaStream_t s) {
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes));
   if (err != cudaSuccess) return err;
-  // two CTAs per SM (108 KiB of shared memory and 128 x 255 registers each), so
+  // two CTAs per SM (108 KiB of shared memory and 256 x 128 registers each), so
   // that one CTA's tile loads and operand stores overlap the other's MMAs
   const int64_t nitems = (d.ntiles + 3) / 4;
   const int grid = int(std::min<int64_t>(nitems, int64_t(2) * sms));
