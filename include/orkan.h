@@ -151,8 +151,10 @@ int orkan_set_fusion(orkan_h h, int max_ops, int compose);
  * dense complex 32 x 32 x 32 products per tile whatever the run's length,
  * run on tcgen05 tensor cores with split-TF32 operands (about 2^-22 relative
  * per pass; complex64 storage holds 2^-24).  Such a run then holds up to 64
- * ops instead of the fusion depth.  mode 0: off (default); 1: runs with at
- * least two dense two-qubit ops or at least six ops; 2: every such run.
+ * ops instead of the fusion depth.  mode 0: off (the default of C128 and
+ * DF64 handles, which it does not serve); 1: runs with at least two dense
+ * two-qubit ops or at least six ops (the default of C64 handles); 2: every
+ * such run.
  * Other handles and ops are unaffected.  A bounded wait inside the pass that
  * runs out makes the next orkan_sync return ORKAN_ETIMEOUT.  Errors: EINVAL. */
 int orkan_set_tensor(orkan_h h, int mode);

@@ -927,6 +927,7 @@ int common_alloc(int n, int dtype, int tile_log2, void* dev_ptr, size_t bytes, o
   c->g = g;
   c->dtype = dtype;
   for (int q = 0; q < 64; ++q) c->phys[q] = c->cap_phys[q] = q;
+  c->tc_mode = dtype == DT_C64 ? 1 : 0;   // tensor-core passes for composed in-tile runs (complex64)
   c->bytes = size_t(g.ntiles) << (2 * g.m);
   c->bytes *= elem_size(dtype);
   cudaGetDevice(&c->device);
