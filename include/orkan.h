@@ -155,7 +155,8 @@ int orkan_set_fusion(orkan_h h, int max_ops, int compose);
  * DF64 handles, which it does not serve); 1: runs with at least two dense
  * two-qubit ops or at least six ops (the default of C64 handles); 2: every
  * such run.
- * Other handles and ops are unaffected.  A bounded wait inside the pass that
+ * A fusion depth of 1 (orkan_set_fusion) keeps the plain one-pass-per-op
+ * path whatever the mode.  Other handles and ops are unaffected.  A bounded wait inside the pass that
  * runs out makes the next orkan_sync return ORKAN_ETIMEOUT.  Errors: EINVAL. */
 int orkan_set_tensor(orkan_h h, int mode);
 

@@ -465,7 +465,8 @@ bool tc_op_ok(const orkan_ctx* h, const HostOp& op) {
 }
 // The pending run may become one tensor-core pass (every op in-tile with a single Kraus operator).
 bool tc_run(const orkan_ctx* h) {
-  if (h->tc_mode == 0 || h->dtype != DT_C64 || h->g.m != 5 || h->pending.empty()) return false;
+  // fusion depth 1 keeps the plain one-pass-per-op path
+  if (h->tc_mode == 0 || h->fusion < 2 || h->dtype != DT_C64 || h->g.m != 5 || h->pending.empty()) return false;
   for (const HostOp& op : h->pending)
     if (!tc_op_ok(h, op)) return false;
   return true;
