@@ -458,7 +458,7 @@ int run_k3(orkan_ctx* h, const HostOp& op) {
 constexpr int kTcMaxOps = 64;
 
 bool tc_op_ok(const orkan_ctx* h, const HostOp& op) {
-  if (!op.has_L || op.nq > 2) return false;
+  if (!op.has_L || op.nq > 3) return false;
   for (int l = 0; l < op.nq; ++l)
     if (op.q[l] >= h->g.m) return false;
   return true;
@@ -476,8 +476,19 @@ bool tc_take(const orkan_ctx* h) {
   if (!tc_run(h)) return false;
   if (h->tc_mode == 2) return true;
   int dense2 = 0;
-  for (const HostOp& op : h->pending) dense2 += op.nq == 2 && op.codes.empty();
+  for (const HostOp& op : h->pending) {
+    if (op.nq == 3) return true;   // a three-qubit op joins a run only as part of a tensor-core pass
+    dense2 += op.nq == 2 && op.codes.empty();
+  }
   return dense2 >= 2 || h->pending.size() >= 6;
+}
+// The pending run can only leave as a tensor-core pass: it is longer than a
+// fused pass holds or holds a three-qubit op.
+bool tc_required(const orkan_ctx* h) {
+  if (int(h->pending.size()) > kMaxOps) return true;
+  for (const HostOp& op : h->pending)
+    if (op.nq == 3) return true;
+  return false;
 }
 
 // L_blk = L_k ... L_1 over the run, each L embedded on the tile's m qubits (FP64).
@@ -540,7 +551,11 @@ int flush_pending(orkan_ctx* h) {
   d.n_tiles = h->g.ntiles;
   if (s.nh == 0) d.n_items = (h->g.ntiles + 3) / 4;
   int slot = 0;
+  double work_per_elem = 0.0;   // algorithmic ALU operations per element of the pass
   for (const HostOp& op : h->pending) {
+    work_per_elem += alu_ops_per_elem(h->dtype, op.nq == 1 && !op.codes.empty() ? OP_MONO1 : op.kind);
+    // native FP64 applies an AD-form map with a real off-diagonal factor in 12 operations per block
+    if (h->dtype == DT_C128 && op.kind == OP_PTM1_AD && op.codes.empty() && op.R[9] == 0.0) work_per_elem -= 1.0;
     PassOp& po = d.ops[d.nops++];
     po.kind = op.kind;
     po.nq = op.nq;
@@ -574,7 +589,7 @@ int flush_pending(orkan_ctx* h) {
   ORKAN_CUDA(launch_pass(h->dtype, h->d_state, d, h->stream, &nlaunch));
   double alu = 0.0;
   const double elems = double(h->g.ntiles) * double(int64_t(1) << (2 * h->g.m));
-  for (int o = 0; o < d.nops; ++o) alu += elems * alu_ops_per_elem(h->dtype, d.ops[o].kind);
+  alu = elems * work_per_elem;
   if (int st = timing_end(h, ev, alu)) return st;
   h->n_passes += 1;
   h->n_ops += nops;
@@ -582,10 +597,22 @@ int flush_pending(orkan_ctx* h) {
   return ORKAN_OK;
 }
 
+bool tc_run(const orkan_ctx* h);
+bool tc_op_ok(const orkan_ctx* h, const HostOp& op);
+bool tc_required(const orkan_ctx* h);
+
 int enqueue(orkan_ctx* h, HostOp op) {
   if (op.nq == 3) {
-    if (int st = flush_pending(h)) return st;
-    return run_k3(h, op);
+    // an in-tile three-qubit single-Kraus op joins a tensor-core run (complex64, m = 5)
+    const bool joins = h->tc_mode != 0 && h->fusion >= 2 && h->dtype == DT_C64 && h->g.m == 5 &&
+                       tc_op_ok(h, op) && (h->pending.empty() || tc_run(h));
+    if (!joins) {
+      if (int st = flush_pending(h)) return st;
+      return run_k3(h, op);
+    }
+    h->pending.push_back(std::move(op));
+    if (int(h->pending.size()) >= kTcMaxOps) return flush_pending(h);
+    return ORKAN_OK;
   }
   // compose consecutive single-qubit ops on the same qubit (FP64, on the host)
   if (h->compose && op.nq == 1 && !h->pending.empty()) {
@@ -602,8 +629,8 @@ int enqueue(orkan_ctx* h, HostOp op) {
       return ORKAN_OK;
     }
   }
-  // a run longer than a fused pass holds can only leave as a tensor-core pass
-  if (!h->pending.empty() && int(h->pending.size()) > kMaxOps && !tc_op_ok(h, op))
+  // a run that can only leave as a tensor-core pass ends before an op that cannot join it
+  if (!h->pending.empty() && tc_required(h) && !tc_op_ok(h, op))
     if (int st = flush_pending(h)) return st;
   if (!fits(h, op)) {
     const int st = flush_pending(h);
@@ -678,6 +705,10 @@ int make_op_adj(bool adj, int k, const int* qubits, const std::vector<Mat>& krau
         for (int j = 0; j < 8; ++j) B[perm(i) * 8 + perm(j)] = K[i * 8 + j];
       // the adjoint map applies L^dagger (.) L = M (.) M^dagger with M = L^dagger
       K = adj ? dagger(B, 8) : B;
+    }
+    if (kraus.size() == 1) {
+      op.L = kraus[0];
+      op.has_L = true;
     }
     std::vector<long long> pp, qq;
     if (unitary && monomial(kraus[0], 8, &pp, &qq)) {

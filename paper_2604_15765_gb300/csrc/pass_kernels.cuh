@@ -159,6 +159,17 @@ __device__ __forceinline__ void body_ptm1_ad(Cx<P>& a, Cx<P>& b, Cx<P>& c, Cx<P>
   const R ai = P::norm(P::mac(P::mul(a.im, al), d.im, be));
   const R dr = P::norm(P::mac(P::mul(a.re, ga), d.re, de));
   const R di = P::norm(P::mac(P::mul(a.im, ga), d.im, de));
+  if constexpr (sizeof(R) == 8) {
+    // native FP64 (2 operations per SM per clock on GB300): the named channels
+    // and projectors scale h01 / h10 by a real factor (sig = 0, uniform over
+    // the warp), which needs 12 instead of 16 FP64 operations per block
+    if (sg == 0.0) {
+      a.re = ar; a.im = ai; d.re = dr; d.im = di;
+      b.re = P::mul(b.re, rh); b.im = P::mul(b.im, rh);
+      c.re = P::mul(c.re, rh); c.im = P::mul(c.im, rh);
+      return;
+    }
+  }
   // h01' = (rho - i sig) h01, h10' = (rho + i sig) h10
   const R br = P::norm(P::mac(P::mul(b.re, rh), b.im, sg));
   const R bi = P::norm(P::mac(P::mul(b.im, rh), P::neg(b.re), sg));

@@ -122,3 +122,23 @@ def test_captured_tensor_pass_replays():
         assert np.max(np.abs(ok.orkan_to_dense(h) - ref)) <= TOL
     finally:
         ok.orkan_free(h)
+
+
+@pytest.mark.parametrize("picture", ["schrodinger", "heisenberg"])
+def test_three_qubit_ops_join_the_tensor_pass(picture):
+    """In-tile three-qubit single-Kraus ops (a Haar unitary, a Toffoli) join
+    the composed block instead of running the block-update kernel on their
+    own; the run is one pass and matches the oracle and the CUDA-core path."""
+    n = 8
+    rng = S.rng_for(6400 + (picture == "heisenberg"))
+    H0 = S.ginibre_state(rng, 1 << n) if picture == "schrodinger" else S.random_hermitian(rng, 1 << n)
+    toffoli = np.eye(8, dtype=np.complex128)[[0, 1, 2, 7, 4, 5, 6, 3]]
+    ops = _intile(rng, n, 4) + [S.op_unitary(S.haar_unitary(rng, 8), [4, 0, 2]),
+                                S.op_unitary(toffoli, [1, 3, 0])] + _intile(rng, n, 3)
+    ref, _ = D.run_circuit(H0, ops, picture)
+    scale = max(1.0, float(np.max(np.abs(ref))))
+    tc, passes = _run(n, ops, 1, picture, H0)
+    cc, _ = _run(n, ops, 0, picture, H0)
+    assert passes == 1
+    assert np.max(np.abs(tc - ref)) <= TOL * scale
+    assert np.max(np.abs(cc - ref)) <= TOL * scale
