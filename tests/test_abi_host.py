@@ -119,3 +119,21 @@ def test_packed_calls_validate_before_any_launch():
         ok.orkan_packed_apply_kraus(64, 3, ok.ORKAN_C128, [0, 1], np.stack([np.eye(4) * 0.5] * 2))  # r > 1, k = 2
     with pytest.raises(ok.OrkanError):
         ok.orkan_packed_depolarize(64, 3, ok.ORKAN_C128, 0, 1.5)
+
+
+def test_batch_and_tensor_entry_points_validate_on_the_host():
+    """orkan_batch_limits checks its arguments without a GPU; an empty batch
+    is a no-op; a NULL handle is refused by orkan_set_tensor."""
+    import ctypes as C
+    with pytest.raises(ok.OrkanError) as e:
+        ok.orkan_batch_limits(-1, 1.0)
+    assert e.value.status == ok.ORKAN_EINVAL
+    with pytest.raises(ok.OrkanError):
+        ok.orkan_batch_limits(0, 0.0)
+    with pytest.raises(ok.OrkanError):
+        ok.orkan_batch_limits(0, 100.0)
+    ok.orkan_batch_limits(4, 0.5)
+    ok.orkan_batch_limits(0, 1.0)
+    assert ok._lib.orkan_run_batch(0, None, None) == ok.ORKAN_OK
+    assert ok._lib.orkan_run_batch(-1, None, None) == ok.ORKAN_EINVAL
+    assert ok._lib.orkan_set_tensor(C.c_void_p(0), 1) == ok.ORKAN_EINVAL
