@@ -255,6 +255,10 @@ struct orkan_ctx {
   int fusion = 8;
   bool compose = true;
   std::vector<HostOp> pending;
+  // single-Kraus single-qubit ops held back, at most one per physical qubit:
+  // the next op on that qubit either absorbs it (a two-qubit single-Kraus op)
+  // or is preceded by it; every flush releases them
+  std::vector<HostOp> held;
   double* d_partials = nullptr;
   double* d_res = nullptr;
   double* h_res = nullptr;   // pinned
@@ -527,7 +531,7 @@ int flush_tc(orkan_ctx* h) {
   return ORKAN_OK;
 }
 
-int flush_pending(orkan_ctx* h) {
+int flush_pass(orkan_ctx* h) {
   if (h->pending.empty()) return ORKAN_OK;
   if (tc_take(h)) return flush_tc(h);
   const PassShape s = shape_of(h, h->pending, nullptr);
@@ -601,17 +605,17 @@ bool tc_run(const orkan_ctx* h);
 bool tc_op_ok(const orkan_ctx* h, const HostOp& op);
 bool tc_required(const orkan_ctx* h);
 
-int enqueue(orkan_ctx* h, HostOp op) {
+int enqueue_now(orkan_ctx* h, HostOp op) {
   if (op.nq == 3) {
     // an in-tile three-qubit single-Kraus op joins a tensor-core run (complex64, m = 5)
     const bool joins = h->tc_mode != 0 && h->fusion >= 2 && h->dtype == DT_C64 && h->g.m == 5 &&
                        tc_op_ok(h, op) && (h->pending.empty() || tc_run(h));
     if (!joins) {
-      if (int st = flush_pending(h)) return st;
+      if (int st = flush_pass(h)) return st;
       return run_k3(h, op);
     }
     h->pending.push_back(std::move(op));
-    if (int(h->pending.size()) >= kTcMaxOps) return flush_pending(h);
+    if (int(h->pending.size()) >= kTcMaxOps) return flush_pass(h);
     return ORKAN_OK;
   }
   // compose consecutive single-qubit ops on the same qubit (FP64, on the host)
@@ -631,15 +635,104 @@ int enqueue(orkan_ctx* h, HostOp op) {
   }
   // a run that can only leave as a tensor-core pass ends before an op that cannot join it
   if (!h->pending.empty() && tc_required(h) && !tc_op_ok(h, op))
-    if (int st = flush_pending(h)) return st;
+    if (int st = flush_pass(h)) return st;
   if (!fits(h, op)) {
-    const int st = flush_pending(h);
+    const int st = flush_pass(h);
     if (st != ORKAN_OK) return st;
   }
   h->pending.push_back(std::move(op));
   const int limit = tc_run(h) ? kTcMaxOps : std::min(h->fusion, kMaxOps);
-  if (int(h->pending.size()) >= limit) return flush_pending(h);
+  if (int(h->pending.size()) >= limit) return flush_pass(h);
   return ORKAN_OK;
+}
+
+// Release the held single-qubit ops (they commute: distinct qubits), in qubit order.
+int release_held(orkan_ctx* h) {
+  std::vector<HostOp> held;
+  held.swap(h->held);
+  std::sort(held.begin(), held.end(), [](const HostOp& a, const HostOp& b) { return a.q[0] < b.q[0]; });
+  for (HostOp& op : held) {
+    h->n_ops -= 1;   // counted when it was held
+    if (int st = enqueue_now(h, std::move(op))) return st;
+  }
+  return ORKAN_OK;
+}
+
+// Every op goes through here.  With fusion and composition on, a
+// single-Kraus single-qubit op is held back; a later single-qubit op on the
+// same qubit composes with it, a single-Kraus two-qubit op on it absorbs it
+// (L2 (L1 (x) I), one 4 x 4 product in FP64: the held op moves forward past
+// ops on other qubits only, with which it commutes), and any other op on it
+// releases it first.  Noisy layered circuits (a single-qubit gate on every
+// qubit, then two-qubit gates on pairs) thus run their single-qubit gates
+// inside the two-qubit ones.
+int enqueue(orkan_ctx* h, HostOp op) {
+  const bool fold = h->compose && h->fusion >= 2;
+  if (!fold) return enqueue_now(h, std::move(op));
+  if (op.nq == 1 && op.has_L) {
+    for (HostOp& held : h->held)
+      if (held.q[0] == op.q[0]) {
+        held.R = mat4mul(op.R, held.R);
+        held.L = matmul(op.L, held.L, 2);
+        held.codes.clear();
+        held.kind = is_unitary_pattern(held.R) ? OP_PTM1_U : (is_ad_pattern(held.R) ? OP_PTM1_AD : OP_PTM1);
+        h->n_ops += 1;
+        return ORKAN_OK;
+      }
+    h->held.push_back(std::move(op));
+    h->n_ops += 1;
+    return ORKAN_OK;
+  }
+  if (op.nq == 2 && op.has_L && op.kind == OP_U2) {   // a permutation gate stays a permutation
+    bool folded = false;
+    for (int l = 0; l < 2; ++l)
+      for (size_t i = 0; i < h->held.size(); ++i)
+        if (h->held[i].q[0] == op.q[l]) {
+          // L <- L (u on local bit l)
+          const Mat& u = h->held[i].L;
+          Mat E(16, 0.0);
+          for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b)
+              if (((a ^ b) & ~(1 << l)) == 0) E[a * 4 + b] = u[((a >> l) & 1) * 2 + ((b >> l) & 1)];
+          op.L = matmul(op.L, E, 4);
+          h->held.erase(h->held.begin() + long(i));
+          folded = true;
+          break;
+        }
+    if (folded) {
+      op.coef.resize(32);
+      for (int i = 0; i < 16; ++i) {
+        op.coef[2 * i] = op.L[i].real();
+        op.coef[2 * i + 1] = op.L[i].imag();
+      }
+    }
+    return enqueue_now(h, std::move(op));
+  }
+  // any other op releases the held ops on its qubits first (a three-qubit op all of them)
+  if (op.nq == 3) {
+    if (int st = release_held(h)) return st;
+    return enqueue_now(h, std::move(op));
+  }
+  for (size_t i = 0; i < h->held.size();) {
+    bool touches = false;
+    for (int l = 0; l < op.nq; ++l) touches |= h->held[i].q[0] == op.q[l];
+    if (touches) {
+      HostOp held = std::move(h->held[i]);
+      h->held.erase(h->held.begin() + long(i));
+      h->n_ops -= 1;
+      if (int st = enqueue_now(h, std::move(held))) return st;
+    } else {
+      ++i;
+    }
+  }
+  return enqueue_now(h, std::move(op));
+}
+
+// Everything issued so far goes to the stream: held ops, then the pending pass.
+int flush_pending(orkan_ctx* h) {
+  if (!h->held.empty())
+    if (int st = release_held(h)) return st;
+  return flush_pass(h);
 }
 
 int check_handle(orkan_h h) {
@@ -1126,6 +1219,7 @@ int orkan_alloc_external(int n, int dtype, int tile_log2, void* dev_ptr, size_t 
 int orkan_free(orkan_h h) {
   if (!h) return ORKAN_OK;
   h->pending.clear();
+  h->held.clear();
   release_handle(h);
   return ORKAN_OK;
 }
@@ -1173,6 +1267,7 @@ void* orkan_device_ptr(orkan_h h) { return h ? h->d_state : nullptr; }
 int orkan_init_state(orkan_h h, int kind, const double* data) {
   if (int st = check_blocking(h)) return st;
   h->pending.clear();
+  h->held.clear();
   reset_labels(h);
   h->picture = ORKAN_STATE;
   switch (kind) {
@@ -1236,6 +1331,7 @@ int orkan_init_observable(orkan_h h, int nterms, const char* paulis, const doubl
   }
   std::stable_sort(terms.begin(), terms.end(), [](const Term& a, const Term& b) { return a.x < b.x; });
   h->pending.clear();
+  h->held.clear();
   reset_labels(h);
   h->picture = ORKAN_OBSERVABLE;
   ORKAN_CUDA(launch_zero(h->dtype, h->d_state, h->g, h->stream));
@@ -1265,6 +1361,7 @@ int orkan_load_tiled(orkan_h h, const void* host_src, int picture) {
   if (int st = check_blocking(h)) return st;
   if (!host_src || (picture != ORKAN_STATE && picture != ORKAN_OBSERVABLE)) return fail(ORKAN_EINVAL, "bad args");
   h->pending.clear();
+  h->held.clear();
   reset_labels(h);
   h->picture = picture;
   ORKAN_CUDA(cudaMemcpyAsync(h->d_state, host_src, h->bytes, cudaMemcpyHostToDevice, h->stream));
@@ -1276,6 +1373,7 @@ int orkan_load_tiled_async(orkan_h h, const void* host_src, int picture) {
   if (int st = check_blocking(h)) return st;
   if (!host_src || (picture != ORKAN_STATE && picture != ORKAN_OBSERVABLE)) return fail(ORKAN_EINVAL, "bad args");
   h->pending.clear();
+  h->held.clear();
   reset_labels(h);
   h->picture = picture;
   ORKAN_CUDA(cudaMemcpyAsync(h->d_state, host_src, h->bytes, cudaMemcpyHostToDevice, h->stream));
@@ -1334,6 +1432,7 @@ int orkan_checkpoint_load(orkan_h h, const void* host_src, size_t bytes) {
                                   ", the handle has n=" + std::to_string(h->g.n) + " tile_log2=" +
                                   std::to_string(h->g.m) + " dtype=" + std::to_string(h->dtype));
   h->pending.clear();
+  h->held.clear();
   const unsigned char* data = static_cast<const unsigned char*>(host_src) + ORKAN_CKPT_HEADER_BYTES;
   ORKAN_CUDA(cudaMemcpyAsync(h->d_state, data, h->bytes, cudaMemcpyHostToDevice, h->stream));
   ORKAN_CUDA(cudaStreamSynchronize(h->stream));
