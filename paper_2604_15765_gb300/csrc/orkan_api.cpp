@@ -534,6 +534,10 @@ int flush_tc(orkan_ctx* h) {
 int flush_pass(orkan_ctx* h) {
   if (h->pending.empty()) return ORKAN_OK;
   if (tc_take(h)) return flush_tc(h);
+  if (tc_required(h)) {   // the planner never builds such a run; refuse rather than overrun the pass descriptor
+    h->pending.clear();
+    return fail(ORKAN_EINVAL, "internal: a run of more than 16 ops or with a three-qubit op is not a tensor-core run");
+  }
   const PassShape s = shape_of(h, h->pending, nullptr);
   // in-tile passes run with four independent tiles per work item, on the
   // one-high-qubit group geometry
@@ -618,6 +622,12 @@ int enqueue_now(orkan_ctx* h, HostOp op) {
     if (int(h->pending.size()) >= kTcMaxOps) return flush_pass(h);
     return ORKAN_OK;
   }
+  // a run that can only leave as a tensor-core pass (longer than a fused pass
+  // holds, or holding a three-qubit op) ends before an op that cannot join
+  // it -- before composition too, which would otherwise merge such an op into
+  // the run's last op and turn the run into an ordinary pass it cannot be
+  if (!h->pending.empty() && tc_required(h) && !tc_op_ok(h, op))
+    if (int st = flush_pass(h)) return st;
   // compose consecutive single-qubit ops on the same qubit (FP64, on the host)
   if (h->compose && op.nq == 1 && !h->pending.empty()) {
     HostOp& last = h->pending.back();
@@ -633,9 +643,6 @@ int enqueue_now(orkan_ctx* h, HostOp op) {
       return ORKAN_OK;
     }
   }
-  // a run that can only leave as a tensor-core pass ends before an op that cannot join it
-  if (!h->pending.empty() && tc_required(h) && !tc_op_ok(h, op))
-    if (int st = flush_pass(h)) return st;
   if (!fits(h, op)) {
     const int st = flush_pass(h);
     if (st != ORKAN_OK) return st;

@@ -142,3 +142,31 @@ def test_three_qubit_ops_join_the_tensor_pass(picture):
     assert passes == 1
     assert np.max(np.abs(tc - ref)) <= TOL * scale
     assert np.max(np.abs(cc - ref)) <= TOL * scale
+
+
+@pytest.mark.parametrize("compose", [True, False])
+def test_long_run_ends_before_a_channel_on_its_last_qubit(compose):
+    """A tensor-core run longer than a fused pass holds (here 20 dense in-tile
+    unitaries) must leave as a tensor-core pass before a channel that cannot
+    join it -- also when the channel would compose into the run's last
+    single-qubit op (a regression: the merged run once became an ordinary
+    pass of more than 16 ops)."""
+    n = 6
+    rng = S.rng_for(6500 + compose)
+    rho = S.ginibre_state(rng, 1 << n)
+    ops = []
+    for _ in range(20):
+        a, b = rng.choice(5, size=2, replace=False)
+        ops.append(S.op_unitary(S.haar_unitary(rng, 4), [int(a), int(b)]))
+    ops += [S.op_unitary(S.haar_unitary(rng, 2), [0]), S.op_unitary(S.haar_unitary(rng, 2), [1]),
+            S.op_ampdamp(0, 0.3), S.op_depolarize(1, 0.1), S.op_unitary(S.haar_unitary(rng, 4), [2, 5])]
+    ref, _ = D.run_circuit(rho, ops)
+    h = ok.orkan_alloc(n, ok.ORKAN_C64, 5)
+    try:
+        ok.orkan_set_fusion(h, 8, compose)
+        ok.orkan_init_state(h, ok.ORKAN_INIT_DENSE, rho)
+        circuit.run_circuit(h, ops)
+        ok.orkan_sync(h)
+        assert np.max(np.abs(ok.orkan_to_dense(h) - ref)) <= TOL
+    finally:
+        ok.orkan_free(h)
