@@ -1688,6 +1688,10 @@ int orkan_run_circuit(orkan_h h, int count, const orkan_op* ops, int* outcomes, 
       default: st = fail(ORKAN_EINVAL, "unknown op kind");
     }
   }
+  // a circuit ends its held single-qubit ops: they join the pending pass (not
+  // yet launched), so a later call cannot absorb them and a circuit's passes
+  // are the same whether it is run directly or recorded and replayed
+  if (st == ORKAN_OK && !h->held.empty()) st = release_held(h);
   if (done) *done = st == ORKAN_OK ? i : i - 1;
   return st;
 }
