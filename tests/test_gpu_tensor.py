@@ -170,3 +170,33 @@ def test_long_run_ends_before_a_channel_on_its_last_qubit(compose):
         assert np.max(np.abs(ok.orkan_to_dense(h) - ref)) <= TOL
     finally:
         ok.orkan_free(h)
+
+
+def test_full_size_tensor_pass_matches_cuda_cores_on_sampled_elements():
+    """n = 13 (32,896 tiles, 269 MB): a 12-op in-tile run as one tensor-core
+    pass against the CUDA-core passes of the same run, on 65,536 sampled
+    elements and the diagonal (the CUDA-core passes are the oracle-checked
+    path at this size)."""
+    n = 13
+    rng = S.rng_for(6600)
+    psi = S.haar_state_vector(rng, 1 << n)
+    ops = _intile(rng, n, 12)
+    N = 1 << n
+    rows = np.concatenate([rng.integers(0, N, 1 << 16), np.arange(N)])
+    cols = np.concatenate([rng.integers(0, N, 1 << 16), np.arange(N)])
+    got = {}
+    for mode in (2, 0):
+        h = ok.orkan_alloc(n, ok.ORKAN_C64, 5)
+        try:
+            ok.orkan_set_tensor(h, mode)
+            ok.orkan_init_state(h, ok.ORKAN_INIT_PURE, psi)
+            p0 = ok.orkan_stats(h)["passes"]
+            circuit.run_circuit(h, ops)
+            ok.orkan_sync(h)
+            if mode == 2:
+                assert ok.orkan_stats(h)["passes"] - p0 == 1
+            got[mode] = ok.orkan_get_elements(h, rows, cols)
+        finally:
+            ok.orkan_free(h)
+    scale = float(np.max(np.abs(got[0])))
+    assert np.max(np.abs(got[2] - got[0])) <= TOL * max(scale, 1e-3)
