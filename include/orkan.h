@@ -138,7 +138,11 @@ int orkan_set_stream(orkan_h h, void *cuda_stream);
 
 /* Fusion policy: at most max_ops (1..16) consecutive ops per pass; compose
  * != 0 lets consecutive single-qubit ops on the same qubit be multiplied
- * into one transfer matrix in FP64 on the host.  Default: 8, 1.
+ * into one transfer matrix in FP64 on the host, and (with max_ops >= 2) holds
+ * single-Kraus single-qubit ops back per qubit so that the next dense
+ * two-qubit single-Kraus op on that qubit absorbs them (one 4 x 4 product in
+ * FP64); any other op on the qubit, the end of an orkan_run_circuit call and
+ * every flush or blocking call release them first.  Default: 8, 1.
  * max_ops = 1 with compose = 0 is the plain one-pass-per-op path. */
 int orkan_set_fusion(orkan_h h, int max_ops, int compose);
 
@@ -154,10 +158,12 @@ int orkan_set_fusion(orkan_h h, int max_ops, int compose);
  * ops instead of the fusion depth.  mode 0: off (the default of C128 and
  * DF64 handles, which it does not serve); 1: runs with at least two dense
  * two-qubit ops or at least six ops (the default of C64 handles); 2: every
- * such run.
- * A fusion depth of 1 (orkan_set_fusion) keeps the plain one-pass-per-op
- * path whatever the mode.  Other handles and ops are unaffected.  A bounded wait inside the pass that
- * runs out makes the next orkan_sync return ORKAN_ETIMEOUT.  Errors: EINVAL. */
+ * such run.  An in-tile three-qubit single-Kraus op joins such a run (it then
+ * always runs as a tensor-core pass).  A fusion depth of 1 (orkan_set_fusion)
+ * keeps the plain one-pass-per-op path whatever the mode.  Other handles and
+ * ops are unaffected.  A bounded wait inside the pass that runs out makes the
+ * next orkan_sync return ORKAN_ETIMEOUT (the operator is then undefined).
+ * Errors: EINVAL. */
 int orkan_set_tensor(orkan_h h, int mode);
 
 int orkan_get_info(orkan_h h, int *n, int *dtype, int *tile_log2, int *picture);
