@@ -70,17 +70,27 @@ __device__ __forceinline__ int64_t bins0(int64_t x, int p) {
   return ((x >> p) << (p + 1)) | low;
 }
 
-// Element access: shared memory (gang 1) or L2-coherent global accesses (gangs).
+// Element access at storage offset o of the tiled array: shared memory (gang
+// 1) or L2-coherent global accesses (gangs).  In shared memory the element
+// index inside each row is XOR-permuted by a hash of the row counter o >> m
+// (bits 0-2, 3-5, 6-8 and 9-11 folded), so that the 2^k rows of a block (rows
+// that differ in the target bits, inside a tile or across tiles) fall in
+// different 16-byte bank groups; the permutation keeps every row in place and
+// is its own inverse.
+__device__ __forceinline__ int64_t swz_off(int64_t o, int m) {
+  const int64_t x = o >> m;
+  return o ^ ((x ^ (x >> 3) ^ (x >> 6) ^ (x >> 9)) & 7);
+}
 template <class P, bool SM>
 struct Acc {
   using E = typename P::Elem;
-  static __device__ __forceinline__ E ld(const E* p) {
-    if constexpr (SM) return *p;
-    else return __ldcg(p);
+  static __device__ __forceinline__ E ld(const E* st, int64_t o, int m) {
+    if constexpr (SM) return st[swz_off(o, m)];
+    else return __ldcg(st + o);
   }
-  static __device__ __forceinline__ void st(E* p, const E& v) {
-    if constexpr (SM) *p = v;
-    else __stcg(p, v);
+  static __device__ __forceinline__ void st(E* st, int64_t o, int m, const E& v) {
+    if constexpr (SM) st[swz_off(o, m)] = v;
+    else __stcg(st + o, v);
   }
 };
 
@@ -96,7 +106,7 @@ template <class P, bool SM>
 __device__ __forceinline__ Cx<P> bread(const typename P::Elem* st, uint64_t i, uint64_t j, int m) {
   bool cj;
   const int64_t o = bloc(i, j, m, cj);
-  const auto e = P::conj_if(Acc<P, SM>::ld(st + o), cj ? 1u : 0u);
+  const auto e = P::conj_if(Acc<P, SM>::ld(st, o, m), cj ? 1u : 0u);
   return Cx<P>{P::re(e), P::im(e)};
 }
 
@@ -105,11 +115,11 @@ __device__ __forceinline__ void bwrite(typename P::Elem* st, uint64_t i, uint64_
   bool cj;
   const int64_t o = bloc(i, j, m, cj);
   const auto e = P::make(v.re, v.im);
-  Acc<P, SM>::st(st + o, P::conj_if(e, cj ? 1u : 0u));
+  Acc<P, SM>::st(st, o, m, P::conj_if(e, cj ? 1u : 0u));
   const uint64_t p = cj ? j : i, q = cj ? i : j;
   if ((p >> m) == (q >> m) && p != q) {
     const uint64_t M1 = (uint64_t(1) << m) - 1;
-    Acc<P, SM>::st(st + (o - int64_t(((p & M1) << m) | (q & M1)) + int64_t(((q & M1) << m) | (p & M1))),
+    Acc<P, SM>::st(st, o - int64_t(((p & M1) << m) | (q & M1)) + int64_t(((q & M1) << m) | (p & M1)), m,
                    P::conj_if(e, cj ? 0u : 1u));
   }
 }
@@ -228,7 +238,7 @@ __device__ void init_pure(const Ctx& c, typename P::Elem* st) {
       re = a.x * b.x + a.y * b.y;
       im = a.y * b.x - a.x * b.y;
     }
-    Acc<P, SM>::st(st + o, Conv<P>::from(re, im));
+    Acc<P, SM>::st(st, o, I.m, Conv<P>::from(re, im));
   }
 }
 
@@ -258,7 +268,7 @@ __device__ void init_pauli_sum(const Ctx& c, typename P::Elem* st) {
         }
       }
     }
-    Acc<P, SM>::st(st + o, Conv<P>::from(re, im));
+    Acc<P, SM>::st(st, o, I.m, Conv<P>::from(re, im));
   }
 }
 
@@ -412,13 +422,13 @@ __device__ void apply_projection(const Ctx& c, typename P::Elem* st, int q, int 
   for (int64_t o = int64_t(c.g) * kBT + threadIdx.x; o < I.stored; o += int64_t(c.G) * kBT) {
     uint64_t i, j;
     decode(o, I.m, i, j);
-    typename P::Elem e = Acc<P, SM>::ld(st + o);
+    typename P::Elem e = Acc<P, SM>::ld(st, o, I.m);
     if (int((i >> q) & 1) != b || int((j >> q) & 1) != b) {
       e = Conv<P>::from(0.0, 0.0);
     } else if (scale != 1.0) {
       e = P::make(P::norm(P::mul(P::re(e), f)), P::norm(P::mul(P::im(e), f)));
     }
-    Acc<P, SM>::st(st + o, e);
+    Acc<P, SM>::st(st, o, I.m, e);
   }
 }
 
@@ -434,7 +444,7 @@ __device__ void run_item(Ctx& c, typename P::Elem* st, typename P::Elem* ybuf, d
   if (I.init == 1) init_pure<P, SM>(c, st);
   else if (I.init == 2) init_pauli_sum<P, SM>(c, st);
   else if (SM)
-    for (int64_t o = threadIdx.x; o < I.stored; o += kBT) st[o] = __ldcg(gst + o);
+    for (int64_t o = threadIdx.x; o < I.stored; o += kBT) st[swz_off(o, I.m)] = __ldcg(gst + o);
   if (!gang_sync(c, s_flag)) return;
   for (int k = I.op_begin; k < I.op_end; ++k) {
     const BatchOp op = d.ops[k];
@@ -452,7 +462,7 @@ __device__ void run_item(Ctx& c, typename P::Elem* st, typename P::Elem* ybuf, d
       const int M = 1 << I.m;
       for (int64_t i = int64_t(c.g) * kBT + threadIdx.x; i < N; i += int64_t(c.G) * kBT) {
         const int64_t t = i >> I.m;
-        const E e = Acc<P, SM>::ld(st + tile_base(t, t, I.m) + (i & (M - 1)) * (M + 1));
+        const E e = Acc<P, SM>::ld(st, tile_base(t, t, I.m) + (i & (M - 1)) * (M + 1), I.m);
         if ((i >> q) & 1) v[1] += P::to_double(P::re(e));
         else v[0] += P::to_double(P::re(e));
       }
@@ -504,7 +514,7 @@ __device__ void run_item(Ctx& c, typename P::Elem* st, typename P::Elem* ybuf, d
       uint64_t i, j;
       decode(o, I.m, i, j);
       if (i >= uint64_t(N) || j >= uint64_t(N) || i < j) continue;
-      const E e = Acc<P, SM>::ld(st + o);
+      const E e = Acc<P, SM>::ld(st, o, I.m);
       const double hr = P::to_double(P::re(e)), hi = P::to_double(P::im(e));
       const double2 a = psi[i], b = psi[j];
       // conj(a) h b
@@ -517,7 +527,7 @@ __device__ void run_item(Ctx& c, typename P::Elem* st, typename P::Elem* ybuf, d
   }
   if (SM) {
     __syncthreads();
-    for (int64_t o = threadIdx.x; o < I.stored; o += kBT) __stcg(gst + o, st[o]);
+    for (int64_t o = threadIdx.x; o < I.stored; o += kBT) __stcg(gst + o, st[swz_off(o, I.m)]);
   }
 }
 
