@@ -25,6 +25,7 @@
 #include "orkan_internal.h"
 #include "numeric.cuh"
 #include "device_util.cuh"
+#include <type_traits>
 
 namespace orkan {
 namespace {
@@ -159,7 +160,7 @@ __device__ __forceinline__ void body_ptm1_ad(Cx<P>& a, Cx<P>& b, Cx<P>& c, Cx<P>
   const R ai = P::norm(P::mac(P::mul(a.im, al), d.im, be));
   const R dr = P::norm(P::mac(P::mul(a.re, ga), d.re, de));
   const R di = P::norm(P::mac(P::mul(a.im, ga), d.im, de));
-  if constexpr (sizeof(R) == 8) {
+  if constexpr (std::is_same<R, double>::value) {
     // native FP64 (2 operations per SM per clock on GB300): the named channels
     // and projectors scale h01 / h10 by a real factor (sig = 0, uniform over
     // the warp), which needs 12 instead of 16 FP64 operations per block
