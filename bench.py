@@ -235,15 +235,27 @@ def alu_peak_tops(dtype: str, sms: int) -> float:
     return sms * UNIT_RATE[dtype] * SM_MAX_HZ / 1e12
 
 
+PASS_SOURCES = ("pass_kernels.cuh", "numeric.cuh", "device_util.cuh")
+
+
+def pass_source_digest() -> str:
+    """First 16 hex digits of the SHA-256 of the pass kernel's device sources,
+    concatenated in PASS_SOURCES order."""
+    h = hashlib.sha256()
+    for name in PASS_SOURCES:
+        with open(os.path.join(ROOT, "paper_2604_15765_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_record(dtype: str):
     """DRAM bytes per pass-kernel launch from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "pass_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_2604_15765_gb300", "csrc", "pass_kernels.cuh")
     try:
         with open(path) as f:
             rec = json.load(f)
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        digest = pass_source_digest()
         ent = rec.get(dtype)
         if ent and ent.get("source_sha256_16") == digest:
             return ent
