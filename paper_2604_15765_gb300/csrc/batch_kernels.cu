@@ -37,6 +37,7 @@
 // Every reduction (Born probabilities, readouts) has a fixed order that
 // depends only on the request's own n and gang size, so a request's results
 // are the same bits alone and in any mix.
+#include <type_traits>
 #include <algorithm>
 #include <cstdint>
 
@@ -71,25 +72,34 @@ __device__ __forceinline__ int64_t bins0(int64_t x, int p) {
 }
 
 // Element access at storage offset o of the tiled array: shared memory (gang
-// 1) or L2-coherent global accesses (gangs).  In shared memory the element
-// index inside each row is XOR-permuted by a hash of the row counter o >> m
-// (bits 0-2, 3-5, 6-8 and 9-11 folded), so that the 2^k rows of a block (rows
-// that differ in the target bits, inside a tile or across tiles) fall in
-// different 16-byte bank groups; the permutation keeps every row in place and
-// is its own inverse.
-__device__ __forceinline__ int64_t swz_off(int64_t o, int m) {
-  const int64_t x = o >> m;
-  return o ^ ((x ^ (x >> 3) ^ (x >> 6) ^ (x >> 9)) & 7);
+// 1) or L2-coherent global accesses (gangs).  In shared memory the FP32-pipe
+// forms (complex64, double-float) XOR-permute the element index inside each
+// row by a hash of the row counter o >> m (bits 0-2, 3-5, 6-8 and 9-11
+// folded), so that the 2^k rows of a block (rows that differ in the target
+// bits, inside a tile or across tiles) fall in different 16-byte bank groups;
+// the permutation keeps every row in place and is its own inverse.  Native
+// FP64 keeps the plain order: there the FP64 pipe binds and the bank
+// conflicts hide behind it, so the permutation's integer work would only add
+// (measured: 16.6 ms plain vs 16.8 ms permuted for 300 requests of n = 4..8,
+// against 12 % less time with the permutation in complex64).
+template <class P>
+__device__ __forceinline__ int64_t sm_off(int64_t o, int m) {
+  if constexpr (std::is_same<typename P::Real, double>::value) {
+    return o;
+  } else {
+    const int64_t x = o >> m;
+    return o ^ ((x ^ (x >> 3) ^ (x >> 6) ^ (x >> 9)) & 7);
+  }
 }
 template <class P, bool SM>
 struct Acc {
   using E = typename P::Elem;
   static __device__ __forceinline__ E ld(const E* st, int64_t o, int m) {
-    if constexpr (SM) return st[swz_off(o, m)];
+    if constexpr (SM) return st[sm_off<P>(o, m)];
     else return __ldcg(st + o);
   }
   static __device__ __forceinline__ void st(E* st, int64_t o, int m, const E& v) {
-    if constexpr (SM) st[swz_off(o, m)] = v;
+    if constexpr (SM) st[sm_off<P>(o, m)] = v;
     else __stcg(st + o, v);
   }
 };
@@ -444,7 +454,7 @@ __device__ void run_item(Ctx& c, typename P::Elem* st, typename P::Elem* ybuf, d
   if (I.init == 1) init_pure<P, SM>(c, st);
   else if (I.init == 2) init_pauli_sum<P, SM>(c, st);
   else if (SM)
-    for (int64_t o = threadIdx.x; o < I.stored; o += kBT) st[swz_off(o, I.m)] = __ldcg(gst + o);
+    for (int64_t o = threadIdx.x; o < I.stored; o += kBT) st[sm_off<P>(o, I.m)] = __ldcg(gst + o);
   if (!gang_sync(c, s_flag)) return;
   for (int k = I.op_begin; k < I.op_end; ++k) {
     const BatchOp op = d.ops[k];
@@ -527,7 +537,7 @@ __device__ void run_item(Ctx& c, typename P::Elem* st, typename P::Elem* ybuf, d
   }
   if (SM) {
     __syncthreads();
-    for (int64_t o = threadIdx.x; o < I.stored; o += kBT) __stcg(gst + o, st[swz_off(o, I.m)]);
+    for (int64_t o = threadIdx.x; o < I.stored; o += kBT) __stcg(gst + o, st[sm_off<P>(o, I.m)]);
   }
 }
 
