@@ -1220,6 +1220,8 @@ int orkan_alloc(int n, int dtype, int tile_log2, orkan_h* out) {
 
 int orkan_alloc_external(int n, int dtype, int tile_log2, void* dev_ptr, size_t bytes, orkan_h* out) {
   if (!dev_ptr) return fail(ORKAN_EINVAL, "null device pointer");
+  // the kernels move 16-byte granules and bulk-prefetch 8 KiB tiles
+  if (reinterpret_cast<uintptr_t>(dev_ptr) & 255u) return fail(ORKAN_EINVAL, "device pointer is not 256-byte aligned");
   return common_alloc(n, dtype, tile_log2, dev_ptr, bytes, out);
 }
 

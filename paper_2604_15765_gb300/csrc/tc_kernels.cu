@@ -177,6 +177,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_kernel(float2* __restrict__ 
                                : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
   };
+  // L2 prefetch of an item's four tiles (contiguous 8 KiB each, one bulk
+  // prefetch per tile by threads 0..3): issued two items ahead, so the
+  // register loads of the next item find their lines in L2
+  auto prefetch_item = [&](int64_t it) {
+    const int64_t tile = it * 4 + t;
+    if (t < 4 && tile < d.ntiles)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], 8192;" :: "l"(st + (tile << 10)) : "memory");
+  };
+  if (int64_t(blockIdx.x) + gridDim.x < nitems) prefetch_item(blockIdx.x + gridDim.x);
   if (int64_t(blockIdx.x) < nitems) load_item(blockIdx.x);
   for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
     const int64_t tile0 = item * 4;
@@ -196,8 +205,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_kernel(float2* __restrict__ 
       asm volatile("tcgen05.fence::after_thread_sync;");
       issue_gemm(d1, ah, al, bh, bl, mb);
     }
-    // the next item's tiles stream in while the tensor cores work
+    // the next item's tiles stream in while the tensor cores work; the one
+    // after it is prefetched into L2
     if (item + gridDim.x < nitems) load_item(item + gridDim.x);
+    if (item + 2 * int64_t(gridDim.x) < nitems) prefetch_item(item + 2 * int64_t(gridDim.x));
     ok = __syncthreads_and(wait_phase(mb, parity));
     parity ^= 1;
     if (!ok) break;

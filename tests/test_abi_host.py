@@ -91,6 +91,15 @@ def test_alloc_without_gpu_reports_no_device():
     assert e.value.status == ok.ORKAN_ENODEV
 
 
+def test_external_buffer_must_be_256_byte_aligned():
+    """orkan_alloc_external refuses a null or unaligned device pointer before
+    touching the device (the kernels move 16-byte granules and 8 KiB tiles)."""
+    for ptr in (0, 0x10008, 0x10010, 0x10080):
+        with pytest.raises(ok.OrkanError) as e:
+            ok.orkan_alloc_external(4, ok.ORKAN_C128, 5, ptr, 1 << 20)
+        assert e.value.status == ok.ORKAN_EINVAL
+
+
 def test_packed_layout_matches_oracle():
     from oracle import packed as PK
     for n in range(1, 12):
