@@ -58,8 +58,13 @@ class HandlePool:
                 self.allocated -= self.nbytes(key[0], key[1])
 
     def acquire(self, n, dtype, count=1, block=True):
-        """count handles for an n-qubit operator, or None if not admissible now."""
+        """count handles for an n-qubit operator, or None if not admissible now.
+        A request that could never fit the budget raises ValueError instead of
+        waiting for memory that will not come."""
         need_each = self.nbytes(n, dtype)
+        if need_each * count > self.budget:
+            raise ValueError(f"{count} operator(s) of n = {n} ({dtype}, {need_each} bytes each) exceed the "
+                             f"memory budget of {self.budget} bytes")
         with self.cv:
             while True:
                 reuse = min(count, len(self.free[(n, dtype)]))

@@ -100,6 +100,17 @@ def test_external_buffer_must_be_256_byte_aligned():
         assert e.value.status == ok.ORKAN_EINVAL
 
 
+def test_serving_pool_refuses_a_request_larger_than_its_budget():
+    """A request whose operators can never fit the memory budget fails at
+    admission (host-side, before any device call) instead of waiting forever."""
+    from paper_2604_15765_gb300 import serving
+    pool = serving.HandlePool(budget_bytes=ok.orkan_bytes(10, ok.ORKAN_C128, 5) + 1)
+    with pytest.raises(ValueError):
+        pool.acquire(11, "c128", 1)
+    with pytest.raises(ValueError):
+        pool.acquire(10, "c128", 2)          # a Heisenberg request holds two operators
+
+
 def test_packed_layout_matches_oracle():
     from oracle import packed as PK
     for n in range(1, 12):
