@@ -172,11 +172,12 @@ def test_long_run_ends_before_a_channel_on_its_last_qubit(compose):
         ok.orkan_free(h)
 
 
-def test_full_size_tensor_pass_matches_cuda_cores_on_sampled_elements():
+def test_full_size_tensor_pass_matches_oracle_on_sampled_elements():
     """n = 13 (32,896 tiles, 269 MB): a 12-op in-tile run as one tensor-core
-    pass against the CUDA-core passes of the same run, on 65,536 sampled
-    elements and the diagonal (the CUDA-core passes are the oracle-checked
-    path at this size)."""
+    pass, on 65,536 sampled elements and the diagonal, against the oracle's
+    factored evaluation of Eq. (1) (the pure initial state stays a single
+    factor under one-operator maps) and against the CUDA-core passes of the
+    same run."""
     n = 13
     rng = S.rng_for(6600)
     psi = S.haar_state_vector(rng, 1 << n)
@@ -184,6 +185,11 @@ def test_full_size_tensor_pass_matches_cuda_cores_on_sampled_elements():
     N = 1 << n
     rows = np.concatenate([rng.integers(0, N, 1 << 16), np.arange(N)])
     cols = np.concatenate([rng.integers(0, N, 1 << 16), np.arange(N)])
+    vecs = [psi]
+    for op in ops:
+        mats = [op["matrix"]] if op["kind"] == "unitary" else op["mats"]
+        vecs = D.apply_kraus_to_factors(vecs, mats, op["qubits"], n)
+    ref = D.factored_elements(vecs, rows, cols)
     got = {}
     for mode in (2, 0):
         h = ok.orkan_alloc(n, ok.ORKAN_C64, 5)
@@ -198,5 +204,6 @@ def test_full_size_tensor_pass_matches_cuda_cores_on_sampled_elements():
             got[mode] = ok.orkan_get_elements(h, rows, cols)
         finally:
             ok.orkan_free(h)
-    scale = float(np.max(np.abs(got[0])))
-    assert np.max(np.abs(got[2] - got[0])) <= TOL * max(scale, 1e-3)
+    scale = max(float(np.max(np.abs(ref))), 1e-3)
+    assert np.max(np.abs(got[2] - ref)) <= TOL * scale
+    assert np.max(np.abs(got[2] - got[0])) <= TOL * scale
