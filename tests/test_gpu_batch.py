@@ -90,6 +90,23 @@ def test_mixed_batch_matches_the_oracle():
             ok.orkan_free(c[0]["h"])
 
 
+def test_largest_gangs_match_the_oracle():
+    """The largest gangs, 64 CTAs (n = 10 in native FP64, automatic; n = 10
+    in complex64, forced), and an automatic 17-CTA double-float gang (n = 10),
+    each group's grid holding its gang whole, against the oracle."""
+    rng = S.rng_for(5150)
+    cases = [_request(rng, 10, ok.ORKAN_C128, "schrodinger"), _request(rng, 10, ok.ORKAN_C64, "heisenberg"),
+             _request(rng, 10, ok.ORKAN_DF64, "schrodinger")]
+    cases[1][0]["gang"] = 64
+    try:
+        res = circuit.run_batch([c[0] for c in cases])
+        for c, r in zip(cases, res):
+            _check(*c, r)
+    finally:
+        for c in cases:
+            ok.orkan_free(c[0]["h"])
+
+
 def test_request_is_bitwise_the_same_alone_and_in_a_mix():
     rng = S.rng_for(5200)
     reqs = [_request(rng, n, ok.ORKAN_C128, pic)[0]
