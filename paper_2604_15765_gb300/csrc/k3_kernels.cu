@@ -123,8 +123,7 @@ __device__ __forceinline__ void k3_term(const Cx<P> (&h)[8], Cx<P> (&acc)[8], ty
 
 // MONO: the monomial form (compile-time, so the Kraus sweep carries no codes).
 template <class P, bool MONO>
-__global__ void __launch_bounds__(kK3Threads) k3_kernel(typename P::Elem* __restrict__ st,
-                                                        const __grid_constant__ K3Desc d) {
+__device__ __forceinline__ void k3_body(typename P::Elem* __restrict__ st, const K3Desc& d) {
   using E = typename P::Elem;
   using R = typename P::Real;
   __shared__ E ybuf[kK3Blocks][64];
@@ -137,15 +136,26 @@ __global__ void __launch_bounds__(kK3Threads) k3_kernel(typename P::Elem* __rest
   auto dep = [&](int x) -> uint64_t {
     return (uint64_t(x & 1) << q0) | (uint64_t((x >> 1) & 1) << q1) | (uint64_t((x >> 2) & 1) << q2);
   };
-  // monomial codes in registers once, outside the loop (p: source index, q: phase)
+  // monomial codes in registers once, outside the loop (p: source index, q:
+  // phase).  With 16-byte elements they are packed, 5 bits per local index x
+  // (p_x in 3 bits, q_x mod 4 in 2), which keeps the form within the 64
+  // registers of four CTAs per SM; 8-byte elements fit there unpacked.
+  constexpr bool kPacked = sizeof(typename P::Elem) == 16;
+  uint64_t codes = 0;
   int pc[8] = {}, qc[8] = {};
   if constexpr (MONO) {
 #pragma unroll
     for (int x = 0; x < 8; ++x) {
-      pc[x] = icoef(d.coef, x);
-      qc[x] = icoef(d.coef, 8 + x);
+      if constexpr (kPacked) {
+        codes |= uint64_t((icoef(d.coef, x) & 7) | ((icoef(d.coef, 8 + x) & 3) << 3)) << (5 * x);
+      } else {
+        pc[x] = icoef(d.coef, x);
+        qc[x] = icoef(d.coef, 8 + x);
+      }
     }
   }
+  auto pcode = [&](int x) { return kPacked ? int(codes >> (5 * x)) & 7 : pc[x]; };
+  auto qcode = [&](int x) { return kPacked ? int(codes >> (5 * x + 3)) & 3 : qc[x]; };
   for (int64_t b = int64_t(blockIdx.x) * kK3Blocks + lb; b < d.nblocks; b += int64_t(gridDim.x) * kK3Blocks) {
     const int64_t s = tri_row(b), sp = b - s * (s + 1) / 2;
     const uint64_t ib = uint64_t(ins0(ins0(ins0(s, q0), q1), q2));
@@ -154,17 +164,24 @@ __global__ void __launch_bounds__(kK3Threads) k3_kernel(typename P::Elem* __rest
 
     if constexpr (MONO) {
       // (L h L^dagger)[a][c] = i^{q_a - q_c} h[p_a][p_c]
-      int pa = pc[0], qa = qc[0];
+      int pa, qa;
+      if constexpr (kPacked) {
+        pa = pcode(a);
+        qa = qcode(a);
+      } else {   // select by the runtime lane index without indexing the register arrays
+        pa = pc[0];
+        qa = qc[0];
 #pragma unroll
-      for (int x = 1; x < 8; ++x)
-        if (a == x) {
-          pa = pc[x];
-          qa = qc[x];
-        }
+        for (int x = 1; x < 8; ++x)
+          if (a == x) {
+            pa = pc[x];
+            qa = qc[x];
+          }
+      }
       const uint64_t isrc = ib | dep(pa);
       Cx<P> v[8];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) v[c] = rot_i<P>(k3_read<P>(st, isrc, jb | dep(pc[c]), m), qa - qc[c]);
+      for (int c = 0; c < 8; ++c) v[c] = rot_i<P>(k3_read<P>(st, isrc, jb | dep(pcode(c)), m), qa - qcode(c));
       __syncwarp(mask);   // every read of the block precedes every write
       const uint64_t i = ib | dep(a);
 #pragma unroll
@@ -192,6 +209,25 @@ __global__ void __launch_bounds__(kK3Threads) k3_kernel(typename P::Elem* __rest
 }
 
 template <class P>
+__global__ void __launch_bounds__(kK3Threads) k3_kernel(typename P::Elem* __restrict__ st,
+                                                        const __grid_constant__ K3Desc d) {
+  k3_body<P, false>(st, d);
+}
+template <class P>
+__global__ void __launch_bounds__(kK3Threads) k3_mono_kernel(typename P::Elem* __restrict__ st,
+                                                             const __grid_constant__ K3Desc d) {
+  k3_body<P, true>(st, d);
+}
+// With 16-byte elements the monomial form is held to 64 registers, i.e. four
+// CTAs per SM, so that more of its gathers are in flight (8-byte elements fit
+// there as they are).
+template <class P>
+__global__ void __launch_bounds__(kK3Threads, 4) k3_mono4_kernel(typename P::Elem* __restrict__ st,
+                                                                 const __grid_constant__ K3Desc d) {
+  k3_body<P, true>(st, d);
+}
+
+template <class P>
 cudaError_t launch_k3_t(void* state, const K3Desc& d, cudaStream_t s) {
   int dev = 0, sms = 0;
   cudaError_t err = cudaGetDevice(&dev);
@@ -199,8 +235,10 @@ cudaError_t launch_k3_t(void* state, const K3Desc& d, cudaStream_t s) {
   if (err != cudaSuccess) return err;
   const int64_t need = (d.nblocks + kK3Blocks - 1) / kK3Blocks;
   const int ctas = int(std::min<int64_t>(need, int64_t(sms) * 8));
-  if (d.form == 1) k3_kernel<P, true><<<ctas, kK3Threads, 0, s>>>(reinterpret_cast<typename P::Elem*>(state), d);
-  else k3_kernel<P, false><<<ctas, kK3Threads, 0, s>>>(reinterpret_cast<typename P::Elem*>(state), d);
+  auto* st = reinterpret_cast<typename P::Elem*>(state);
+  if (d.form != 1) k3_kernel<P><<<ctas, kK3Threads, 0, s>>>(st, d);
+  else if constexpr (sizeof(typename P::Elem) == 16) k3_mono4_kernel<P><<<ctas, kK3Threads, 0, s>>>(st, d);
+  else k3_mono_kernel<P><<<ctas, kK3Threads, 0, s>>>(st, d);
   return cudaGetLastError();
 }
 
